@@ -1,0 +1,191 @@
+/*
+ * fnt_rs.h -- C ABI of libfntrs.so: FNT-based Reed-Solomon erasure codes
+ * over the Fermat prime field F_65537 on one GB300 GPU (sm_103a).
+ *
+ * Method: Soro & Lacan, "FNT-based Reed-Solomon Erasure Codes".
+ *   - field and root of unity: Sec. II.A (3 is a primitive root of GF(65537))
+ *     and Sec. II.B (r = 3^(2^(16-i)) has order n = 2^i);
+ *   - non-systematic encoding e_i = s(r^i), i < n, by one FNT of the
+ *     zero-padded source: Sec. II.B;
+ *   - erasure decoding by interpolation, steps 1-6 of Sec. II.B: per erasure
+ *     pattern A(x) = prod (x - x_i), A'(x_i); per codeword n_i = v_i / A'(x_i),
+ *     the power series sum n_i / (x - x_i) by one FNT, and the product with A;
+ *   - per-pattern work done once for many codewords: Sec. II.B (last part).
+ *
+ * Data layout (all buffers are owned by the caller; Sec. II.B interleaving):
+ *   a batch of W codewords is a row-major matrix whose column c is codeword c.
+ *     source   src[k][ld_src]   uint16  (row i = source symbol i / packet i)
+ *     encoded  enc[n][ld_enc]   uint32  values in [0, 65536]
+ *     received recv[npos][ld]   uint32  row i = symbols received at positions[i]
+ *     decoded  out[k][ld_out]   uint16
+ *   Leading dimensions are in elements, ld >= W.  Device pointers must be
+ *   4-byte aligned for uint16 buffers when W is even, 4-byte aligned for
+ *   uint32 buffers.
+ *
+ * Streams: every `stream` argument is a cudaStream_t passed as void*
+ * (NULL = legacy default stream).  Calls enqueue work and return without
+ * synchronising, except where noted.
+ *
+ * Errors: every int-returning call returns FNT_RS_OK (0) or a negative
+ * FNT_RS_E_* code; no exception crosses the ABI.  Argument errors are
+ * detected on the host before any launch.  Data-dependent conditions found
+ * on the device (a decoded coefficient equal to 65536, a received value above
+ * 65536, a device wait that gave up) are ORed into a per-plan status word that
+ * fnt_rs_status() reads and clears.
+ *
+ * Allocation: plan creation allocates the plan's device tables; encode,
+ * decode and FNT calls never allocate -- their scratch is the caller's
+ * `workspace` of fnt_rs_workspace_bytes() bytes (may be NULL when that size
+ * is 0).  A decode with a new erasure pattern builds the pattern's tables into
+ * plan-owned buffers reserved at plan creation.
+ *
+ * Thread safety: a plan may be used from one host thread at a time.
+ */
+#ifndef FNT_RS_H
+#define FNT_RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FNT_RS_P 65537u
+
+enum fnt_rs_status_code {
+  FNT_RS_OK = 0,
+  FNT_RS_E_ARG = -1,            /* bad pointer, size, alignment or leading dimension */
+  FNT_RS_E_UNSUPPORTED_P = -2,  /* p != 65537 */
+  FNT_RS_E_ROOT = -3,           /* root does not have order exactly n */
+  FNT_RS_E_POSITIONS = -4,      /* fewer than k positions, a duplicate, or one >= n */
+  FNT_RS_E_BUDGET = -5,         /* admission refused: request exceeds the memory budget */
+  FNT_RS_E_CUDA = -6,           /* a CUDA runtime call failed */
+  FNT_RS_E_RANGE = -7,          /* status: decoded 65536 (written as 0) or received > 65536 */
+  FNT_RS_E_TIMEOUT = -8,        /* status: a bounded device wait gave up */
+  FNT_RS_E_WORKSPACE = -9       /* workspace missing or too small */
+};
+
+enum fnt_rs_op {
+  FNT_RS_OP_ENCODE = 0,
+  FNT_RS_OP_DECODE = 1,
+  FNT_RS_OP_FNT = 2,
+  FNT_RS_OP_ENCODE_HOST = 3,    /* fnt_rs_encode_host staging */
+  FNT_RS_OP_DECODE_HOST = 4     /* fnt_rs_decode_host staging */
+};
+
+typedef struct fnt_rs_plan_s* fnt_rs_plan;
+
+/*
+ * Create a plan for codes of length n and dimension k over F_p.
+ *   n     : power of two, 2 <= n <= 65536 (Sec. II.B: n = 2^i, n < 65537)
+ *   k     : 1 <= k <= n (Sec. II.B: k <= n; k need not be a power of two)
+ *   p     : must be 65537, else FNT_RS_E_UNSUPPORTED_P
+ *   root  : 0 selects the paper's r = 3^(65536/n) (Sec. II.B); any other value
+ *           must have order exactly n, else FNT_RS_E_ROOT.  Other roots
+ *           define other (still MDS) codes.
+ *   stream: stream on which the plan's tables are uploaded.
+ * On success *out owns device tables until fnt_rs_plan_destroy.
+ */
+int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p, uint32_t root,
+                       void* stream);
+
+/* Synchronises the device, then frees the plan and its device tables. NULL is a no-op. */
+void fnt_rs_plan_destroy(fnt_rs_plan plan);
+
+/* Bytes of device workspace a call of kind `op` (enum fnt_rs_op) needs for W codewords. */
+size_t fnt_rs_workspace_bytes(fnt_rs_plan plan, size_t W, int op);
+
+/*
+ * Non-systematic encode (Sec. II.B): enc[j][c] = s_c(r^j) for j < n, c < W,
+ * where s_c(x) = sum_{i<k} src[i][c] x^i.  Output values lie in [0, 65536].
+ * src, enc: device pointers; workspace: device, fnt_rs_workspace_bytes(plan,
+ * W, FNT_RS_OP_ENCODE) bytes.  Enqueued on `stream`.
+ */
+int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                  size_t ld_enc, size_t W, void* workspace, void* stream);
+
+/*
+ * Per-pattern preparation, steps 1-3 of the interpolation (Sec. II.B):
+ * from the first k of `positions` (host array, npos >= k entries, distinct,
+ * each < n) build on the device A(x) = prod (x - r^z_i), the weights
+ * -r^(-z_i) / A'(r^z_i) and the transform of A mod x^k used by step 6.
+ * Cached per plan: a later decode with the same first k positions reuses it.
+ * Enqueued on `stream`; the host array may be reused when the call returns.
+ */
+int fnt_rs_decode_prepare(fnt_rs_plan plan, const uint32_t* positions, uint32_t npos,
+                          void* stream);
+
+/*
+ * Erasure decode (Sec. II.B, steps 4-6 per codeword; steps 1-3 through the
+ * pattern cache): out[j][c], j < k, are the coefficients of the unique
+ * polynomial of degree < k through (r^positions[i], recv[i][c]), i < k.
+ * recv: device [npos][ld_recv] uint32 (rows beyond k are ignored);
+ * positions: host; out: device [k][ld_out] uint16.  A coefficient equal to
+ * 65536, which no 16-bit source symbol has, is written as 0 and raises
+ * FNT_RS_E_RANGE in the status word, as does a received value above 65536.
+ * With all n positions received this is the inverse FNT's first k outputs
+ * (Sec. II.B).
+ */
+int fnt_rs_decode(fnt_rs_plan plan, const uint32_t* recv, size_t ld_recv,
+                  const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
+                  size_t W, void* workspace, void* stream);
+
+/*
+ * Erasure decode from a receiver's slot buffer (Sec. II.B, same steps as
+ * fnt_rs_decode): slots is a device [n][ld_slots] uint32 matrix whose row z
+ * holds the symbols received at position z (rows of erased positions are
+ * never read).  Only the first k entries of `positions` are used.  Plans with
+ * a non-default root return FNT_RS_E_ROOT (their positions are not slot rows).
+ */
+int fnt_rs_decode_slots(fnt_rs_plan plan, const uint32_t* slots, size_t ld_slots,
+                        const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
+                        size_t W, void* workspace, void* stream);
+
+/*
+ * Batched FNT of length n (Sec. II.A): out[j][c] = sum_i in[i][c] r^(ij)
+ * (inverse = 0) or n^-1 sum_i in[i][c] r^(-ij) (inverse = 1), all mod p,
+ * outputs in [0, 65536].  in, out: device [n][ld] uint32 with values in
+ * [0, 2^32) taken mod p; in and out must not overlap.
+ */
+int fnt_rs_fnt(fnt_rs_plan plan, const uint32_t* in, size_t ld_in, uint32_t* out, size_t ld_out,
+               size_t W, int inverse, void* workspace, void* stream);
+
+/*
+ * Host-buffer variants: same results as fnt_rs_encode / fnt_rs_decode with
+ * host source and destination buffers (pinned memory gives asynchronous
+ * copies).  The host-to-device copy, the kernels and the device-to-host copy
+ * are enqueued on `stream` and the call synchronises the stream before
+ * returning.  workspace: device, fnt_rs_workspace_bytes(plan, W,
+ * FNT_RS_OP_ENCODE_HOST / FNT_RS_OP_DECODE_HOST) bytes; it also stages the
+ * data.  Host buffers are dense (ld = W).
+ */
+int fnt_rs_encode_host(fnt_rs_plan plan, const uint16_t* h_src, uint32_t* h_enc, size_t W,
+                       void* workspace, void* stream);
+int fnt_rs_decode_host(fnt_rs_plan plan, const uint32_t* h_recv, const uint32_t* positions,
+                       uint32_t npos, uint16_t* h_out, size_t W, void* workspace, void* stream);
+
+/*
+ * Reads the plan's device status word (synchronising `stream`), clears it and
+ * returns FNT_RS_OK, FNT_RS_E_RANGE or FNT_RS_E_TIMEOUT (the most severe seen).
+ */
+int fnt_rs_status(fnt_rs_plan plan, void* stream);
+
+/* Static description of a status code. */
+const char* fnt_rs_strerror(int code);
+
+/* Number of kernel launches the library has issued since load (all plans). */
+uint64_t fnt_rs_launch_count(void);
+
+/*
+ * Plan introspection for tuning and tests: writes up to `cap` ints
+ * {n, k, L, C, Wt_encode, Wt_decode, schedule_id, pattern_cache_entries}.
+ * Returns the number written.
+ */
+int fnt_rs_plan_info(fnt_rs_plan plan, int* info, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNT_RS_H */

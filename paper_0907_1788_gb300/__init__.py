@@ -1,0 +1,240 @@
+"""GB300-native FNT-based Reed-Solomon erasure codes over F_65537.
+
+Python binding of ``libfntrs.so`` (C ABI in ``include/fnt_rs.h``).  The
+functions below carry the C names and only marshal arguments: torch tensors
+supply device memory and streams, every arithmetic step runs in the library's
+CUDA kernels.  There is no CPU path.
+
+Layout (Sec. II.B interleaving): a batch of W codewords is a row-major
+``[rows][W]`` tensor whose column c is codeword c --
+source ``[k][W]`` 16-bit, encoded ``[n][W]`` 32-bit (values 0..65536),
+received ``[npos][W]`` 32-bit, decoded ``[k][W]`` 16-bit.  Any torch dtype of
+the right width works (the library reads raw bits); the helpers allocate
+int16 / int32 tensors, which torch supports fully, holding the unsigned values.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import FntRsError, LIB_PATH, load  # noqa: F401
+
+P = 65537
+OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
+
+E_RANGE = -7
+E_TIMEOUT = -8
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise FntRsError(rc, what)
+
+
+def _cols(t: torch.Tensor):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D row-major tensor with unit column stride")
+    return t.shape[1], t.stride(0)
+
+
+def _positions(positions) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(positions, dtype=np.uint32))
+
+
+def fnt_rs_plan_create(n: int, k: int, p: int = P, root: int = 0, stream=None) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.fnt_rs_plan_create(ctypes.byref(h), n, k, p, root, _stream(stream)),
+           "fnt_rs_plan_create")
+    return h.value
+
+
+def fnt_rs_plan_destroy(plan: int) -> None:
+    load().fnt_rs_plan_destroy(plan)
+
+
+def fnt_rs_workspace_bytes(plan: int, W: int, op: int) -> int:
+    return int(load().fnt_rs_workspace_bytes(plan, W, op))
+
+
+def fnt_rs_encode(plan, src: torch.Tensor, enc: torch.Tensor, workspace=None, stream=None):
+    W, ld_src = _cols(src)
+    W2, ld_enc = _cols(enc)
+    if W2 != W:
+        raise ValueError("src and enc must have the same number of columns")
+    _check(load().fnt_rs_encode(plan, _ptr(src), ld_src, _ptr(enc), ld_enc, W, _ptr(workspace),
+                                _stream(stream)), "fnt_rs_encode")
+
+
+def fnt_rs_decode_prepare(plan, positions, stream=None):
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode_prepare(plan, pos.ctypes.data, len(pos), _stream(stream)),
+           "fnt_rs_decode_prepare")
+
+
+def fnt_rs_decode(plan, recv: torch.Tensor, positions, out: torch.Tensor, workspace=None,
+                  stream=None):
+    W, ld_recv = _cols(recv)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("recv and out must have the same number of columns")
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode(plan, _ptr(recv), ld_recv, pos.ctypes.data, len(pos), _ptr(out),
+                                ld_out, W, _ptr(workspace), _stream(stream)), "fnt_rs_decode")
+
+
+def fnt_rs_decode_slots(plan, slots: torch.Tensor, positions, out: torch.Tensor, workspace=None,
+                        stream=None):
+    W, ld = _cols(slots)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("slots and out must have the same number of columns")
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode_slots(plan, _ptr(slots), ld, pos.ctypes.data, len(pos), _ptr(out),
+                                      ld_out, W, _ptr(workspace), _stream(stream)),
+           "fnt_rs_decode_slots")
+
+
+def fnt_rs_fnt(plan, x: torch.Tensor, out: torch.Tensor, inverse: bool = False, workspace=None,
+               stream=None):
+    W, ld_in = _cols(x)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("in and out must have the same number of columns")
+    _check(load().fnt_rs_fnt(plan, _ptr(x), ld_in, _ptr(out), ld_out, W, int(bool(inverse)),
+                             _ptr(workspace), _stream(stream)), "fnt_rs_fnt")
+
+
+def fnt_rs_encode_host(plan, h_src: torch.Tensor, h_enc: torch.Tensor, workspace, stream=None):
+    W = h_src.shape[1]
+    _check(load().fnt_rs_encode_host(plan, _ptr(h_src), _ptr(h_enc), W, _ptr(workspace),
+                                     _stream(stream)), "fnt_rs_encode_host")
+
+
+def fnt_rs_decode_host(plan, h_recv: torch.Tensor, positions, h_out: torch.Tensor, workspace,
+                       stream=None):
+    W = h_recv.shape[1]
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode_host(plan, _ptr(h_recv), pos.ctypes.data, len(pos), _ptr(h_out),
+                                     W, _ptr(workspace), _stream(stream)), "fnt_rs_decode_host")
+
+
+def fnt_rs_status(plan, stream=None) -> int:
+    return int(load().fnt_rs_status(plan, _stream(stream)))
+
+
+def fnt_rs_strerror(code: int) -> str:
+    return load().fnt_rs_strerror(code).decode()
+
+
+def fnt_rs_launch_count() -> int:
+    return int(load().fnt_rs_launch_count())
+
+
+def fnt_rs_plan_info(plan) -> dict:
+    buf = (ctypes.c_int * 8)()
+    m = load().fnt_rs_plan_info(plan, buf, 8)
+    keys = ["n", "k", "L", "C", "wt_one", "wt_two", "blocked", "patterns"]
+    return {keys[i]: int(buf[i]) for i in range(m)}
+
+
+class Plan:
+    """Owns a plan handle; allocates outputs and workspace with torch (plumbing only)."""
+
+    def __init__(self, n: int, k: int, root: int = 0, device=None, stream=None):
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.handle = fnt_rs_plan_create(n, k, P, root, stream)
+        self.n, self.k = n, k
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fnt_rs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, W: int, op: int):
+        nbytes = fnt_rs_workspace_bytes(self.handle, W, op)
+        if nbytes == 0:
+            return None
+        ws = self._ws.get(op)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._ws[op] = ws
+        return ws
+
+    def encode(self, src: torch.Tensor, out=None, stream=None):
+        W = src.shape[1]
+        if out is None:
+            out = torch.empty((self.n, W), dtype=torch.int32, device=src.device)
+        fnt_rs_encode(self.handle, src, out, self.workspace(W, OP_ENCODE), stream)
+        return out
+
+    def prepare(self, positions, stream=None):
+        fnt_rs_decode_prepare(self.handle, positions, stream)
+
+    def decode(self, recv: torch.Tensor, positions, out=None, stream=None):
+        W = recv.shape[1]
+        if out is None:
+            out = torch.empty((self.k, W), dtype=torch.int16, device=recv.device)
+        fnt_rs_decode(self.handle, recv, positions, out, self.workspace(W, OP_DECODE), stream)
+        return out
+
+    def decode_slots(self, slots: torch.Tensor, positions, out=None, stream=None):
+        W = slots.shape[1]
+        if out is None:
+            out = torch.empty((self.k, W), dtype=torch.int16, device=slots.device)
+        fnt_rs_decode_slots(self.handle, slots, positions, out, self.workspace(W, OP_DECODE),
+                            stream)
+        return out
+
+    def fnt(self, x: torch.Tensor, inverse: bool = False, out=None, stream=None):
+        W = x.shape[1]
+        if out is None:
+            out = torch.empty((self.n, W), dtype=torch.int32, device=x.device)
+        fnt_rs_fnt(self.handle, x, out, inverse, self.workspace(W, OP_FNT), stream)
+        return out
+
+    def status(self, stream=None) -> int:
+        return fnt_rs_status(self.handle, stream)
+
+    def info(self) -> dict:
+        return fnt_rs_plan_info(self.handle)
+
+
+def to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    """Upload a uint16 / uint32 numpy array as an int16 / int32 tensor (same bits)."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).to(device)
+
+
+def to_host(t: torch.Tensor) -> np.ndarray:
+    """Download an int16 / int32 tensor as uint16 / uint32 numpy (same bits)."""
+    a = t.detach().cpu().numpy()
+    if a.dtype == np.int16:
+        return a.view(np.uint16)
+    if a.dtype == np.int32:
+        return a.view(np.uint32)
+    return a

@@ -1,0 +1,139 @@
+// Device arithmetic for F_65537 (Sec. II.A/II.B: p = 2^16 + 1, 3 is a
+// primitive root, roots of order n = 2^i are 3^(2^(16-i))).
+//
+// Representation.  p divides M = 2^32 - 1 (2^16 = -1 mod p, so 2^32 = 1), and
+// reduction mod p is a ring homomorphism Z/M -> F_p.  The kernels therefore
+// compute in Z/M on plain 32-bit words and reduce to [0, p) only when a
+// value leaves the GPU:
+//   add / sub  : 32-bit add / sub with the carry (borrow) folded back in,
+//   x * 2^j    : a 32-bit rotation (x * 2^32 = x in Z/M), one instruction --
+//                every root of order <= 32 is a power of two mod p
+//                (r_2 = 2^16, r_4 = 2^24, r_8 = 2^12, r_16 = 2^6, r_32 = 2^19),
+//   x * w      : 32x32 -> 64-bit product, high word added back (2^32 = 1).
+// Any 32-bit word is a valid element; the source's 16-bit symbols and the
+// encoded 17-bit symbols are used as they are.
+#pragma once
+#include <stdint.h>
+
+namespace fntrs {
+
+constexpr uint32_t kP = 65537u;
+
+__device__ __forceinline__ uint32_t m_add(uint32_t a, uint32_t b) {
+  uint32_t s;
+  asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, t, 0;\n\t}"
+      : "=r"(s) : "r"(a), "r"(b));
+  return s;
+}
+
+__device__ __forceinline__ uint32_t m_sub(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\tsubc.u32 %0, t, 0;\n\t}"
+      : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// x * 2^s in Z/M (s in [0, 32))
+template <int S>
+__device__ __forceinline__ uint32_t m_rot(uint32_t x) {
+  if constexpr ((S & 31) == 0) {
+    return x;
+  } else {
+    return __funnelshift_l(x, x, S & 31);
+  }
+}
+
+__device__ __forceinline__ uint32_t m_rot_rt(uint32_t x, uint32_t s) {
+  return __funnelshift_l(x, x, s & 31u);
+}
+
+// x * w in Z/M for any 32-bit x and w < 2^17
+__device__ __forceinline__ uint32_t m_mul(uint32_t x, uint32_t w) {
+  return m_add(x * w, __umulhi(x, w));
+}
+
+// Reduce an element of Z/M to its representative in [0, p) = [0, 65536].
+__device__ __forceinline__ uint32_t m_to_p(uint32_t x) {
+  int32_t t = (int32_t)(x & 0xFFFFu) - (int32_t)(x >> 16);
+  return (uint32_t)(t + ((t >> 31) & (int32_t)kP));
+}
+
+// Exponentiation in F_p (canonical inputs < p); used for per-pattern inverses.
+__device__ __forceinline__ uint32_t p_mul(uint32_t a, uint32_t b) {
+  return m_to_p(m_mul(a, b));
+}
+
+__device__ __forceinline__ uint32_t p_pow(uint32_t a, uint32_t e) {
+  uint32_t r = 1, b = m_to_p(a);
+  while (e) {
+    if (e & 1u) r = p_mul(r, b);
+    b = p_mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Fermat inverse a^(p-2); 0 maps to 0.
+__device__ __forceinline__ uint32_t p_inv(uint32_t a) { return p_pow(a, kP - 2); }
+
+// Exponent e_R with r_R = 2^(e_R) mod p for R <= 32 (derived from 3^(65536/R)).
+template <int R>
+struct Pow2Root;
+template <> struct Pow2Root<1> { static constexpr int e = 0; };
+template <> struct Pow2Root<2> { static constexpr int e = 16; };
+template <> struct Pow2Root<4> { static constexpr int e = 24; };
+template <> struct Pow2Root<8> { static constexpr int e = 12; };
+template <> struct Pow2Root<16> { static constexpr int e = 6; };
+template <> struct Pow2Root<32> { static constexpr int e = 19; };
+
+constexpr int bitrev(int v, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+constexpr int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+// In-register radix-R DFT over Z/M, decimation in frequency:
+//   X[j] = sum_i x[i] w^(ij), w = 2^E a root of order R (E = e_R, or 32 - e_R
+//   for the inverse), natural input order, output X[j] in x[bitrev(j)].
+// The (a - b) * 2^16 products use b - a instead (2^16 = -1 mod p).
+template <int R, int OFF, int E>
+struct DifReg {
+  static __device__ __forceinline__ void run(uint32_t* x) {
+    constexpr int H = R / 2;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const uint32_t a = x[OFF + i], b = x[OFF + i + H];
+      x[OFF + i] = m_add(a, b);
+      const int s = (E * i) & 31;
+      if (s == 0) {
+        x[OFF + i + H] = m_sub(a, b);
+      } else if (s == 16) {
+        x[OFF + i + H] = m_sub(b, a);
+      } else if (s > 16) {
+        x[OFF + i + H] = m_rot_rt(m_sub(b, a), s - 16);
+      } else {
+        x[OFF + i + H] = m_rot_rt(m_sub(a, b), s);
+      }
+    }
+    DifReg<H, OFF, (2 * E) & 31>::run(x);
+    DifReg<H, OFF + H, (2 * E) & 31>::run(x);
+  }
+};
+template <int OFF, int E>
+struct DifReg<1, OFF, E> {
+  static __device__ __forceinline__ void run(uint32_t*) {}
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(uint32_t* x) {
+  constexpr int e = Pow2Root<R>::e;
+  DifReg<R, 0, INV ? ((32 - e) & 31) : e>::run(x);
+}
+
+}  // namespace fntrs

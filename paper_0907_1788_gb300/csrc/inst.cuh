@@ -1,0 +1,100 @@
+// Launch wrappers for the kernel templates (included by the instantiation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "sched.h"
+
+namespace fntrs {
+
+void count_launch();
+
+template <int L> struct SchedFor { using type = Sched<L, L>; };
+template <> struct SchedFor<64> { using type = Sched<64, 8, 8>; };
+template <> struct SchedFor<128> { using type = Sched<128, 16, 8>; };
+template <> struct SchedFor<256> { using type = Sched<256, 16, 16>; };
+template <> struct SchedFor<512> { using type = Sched<512, 32, 16>; };
+template <> struct SchedFor<1024> { using type = Sched<1024, 32, 32>; };
+template <> struct SchedFor<2048> { using type = Sched<2048, 16, 16, 8>; };
+template <> struct SchedFor<4096> { using type = Sched<4096, 16, 16, 16>; };
+template <> struct SchedFor<8192> { using type = Sched<8192, 32, 16, 16>; };
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <class Tag>
+inline void ensure_smem(void (*kern)(KArgs), int bytes) {
+  static bool done[64] = {};
+  if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!done[dev & 63]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done[dev & 63] = true;
+  }
+}
+
+template <class S, int WT, int NT, bool INV, class LD, class ST>
+void launch_tile(const KArgs& a, int gy, cudaStream_t st) {
+  auto kern = k_tile<S, WT, NT, INV, LD, ST>;
+  const int smem = S::NP >= 2 ? S::L * WT * 4 : 0;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  dim3 grid((a.W + WT - 1) / WT, gy);
+  kern<<<grid, NT, smem, st>>>(a);
+  count_launch();
+}
+
+template <class S, int WT, int NT>
+void launch_decode(const KArgs& a, int, cudaStream_t st) {
+  auto kern = k_decode<S, WT, NT>;
+  const int smem = S::NP >= 2 ? S::L * WT * 4 : 0;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  dim3 grid((a.W + WT - 1) / WT, 1);
+  kern<<<grid, NT, smem, st>>>(a);
+  count_launch();
+}
+
+template <class S, int WT, int NT>
+void launch_decode_split(const KArgs& a, int, cudaStream_t st) {
+  auto kern = k_decode_split<S, WT, NT>;
+  const int smem = 2 * S::L * WT * 4;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  dim3 grid((a.W + WT - 1) / WT, 1);
+  kern<<<grid, NT, smem, st>>>(a);
+  count_launch();
+}
+
+template <class S, int WT, int NT>
+void launch_poly_level(const KArgs& a, int, cudaStream_t st) {
+  auto kern = k_poly_level<S, WT, NT>;
+  const int smem = 2 * S::L * WT * 4;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  const int npairs = (a.nodes + 1) / 2;
+  dim3 grid((npairs + WT - 1) / WT, 1);
+  kern<<<grid, NT, smem, st>>>(a);
+  count_launch();
+}
+
+template <int L>
+TileOps make_tile_ops() {
+  using S = typename SchedFor<L>::type;
+  constexpr int W1 = wt_one(L), W2 = wt_two(L), NT = nt_for(L);
+  TileOps ops;
+  ops.L = L;
+  ops.wt1 = W1;
+  ops.wt2 = W2;
+  ops.nt = NT;
+  ops.encode = &launch_tile<S, W1, NT, false, LoadSrcFold<W1>, StoreRows32<W1>>;
+  ops.fnt_fwd = &launch_tile<S, W1, NT, false, LoadRows32<W1>, StoreRows32<W1>>;
+  ops.fnt_inv = &launch_tile<S, W1, NT, true, LoadRows32<W1>, StoreRows32<W1>>;
+  ops.decode = &launch_decode<S, W1, NT>;
+  ops.decode_split = &launch_decode_split<S, W2, NT>;
+  if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;
+  return ops;
+}
+
+void register_ops(const TileOps& ops);
+
+}  // namespace fntrs

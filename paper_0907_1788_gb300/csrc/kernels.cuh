@@ -1,0 +1,624 @@
+// Kernel templates: encode, batched FNT, split-transform cross / local passes,
+// fused single-CTA decode, and one level of the locator product tree.
+#pragma once
+#include "kargs.h"
+#include "tile.cuh"
+
+namespace fntrs {
+
+// ---------------------------------------------------------------------------
+// Loaders: element i (0 <= i < L) of tile codeword c.
+// ---------------------------------------------------------------------------
+
+// Encode input (Sec. II.B: the FNT of (s_0..s_{k-1}, 0..0)).  For a transform
+// split as n = C * L the CTA of output class cc (outputs j = cc + C*j') feeds
+// the length-L transform with  x[i] = r_n^(i*cc) * sum_m s[i + m L] w_C^(m*cc),
+// w_C = r_n^L = 2^(e_C) (a rotation); for C = 1 this is the zero-padded source.
+template <int WT>
+struct LoadSrcFold {
+  const uint16_t* src;
+  size_t ld;
+  const uint32_t* powf;
+  int col0, W, k, L, C, cc, eC, nmask;
+  static __device__ __forceinline__ LoadSrcFold make(const KArgs& a) {
+    int eC = 0;
+    for (int c = a.C; c > 1; c >>= 1) eC += 1;  // log2(C)
+    // e_C for C = 2,4,8,16: 16, 24, 12, 6  (2^e_C = 3^(65536/C) mod p)
+    const int tab[5] = {0, 16, 24, 12, 6};
+    return LoadSrcFold{static_cast<const uint16_t*>(a.in), a.ld_in, a.powf,
+                       (int)blockIdx.x * WT, a.W, a.k, a.L, a.C, (int)blockIdx.y,
+                       tab[eC], a.n - 1};
+  }
+  __device__ __forceinline__ uint32_t operator()(int i, int c) const {
+    const int col = col0 + c;
+    if (col >= W) return 0u;
+    uint32_t acc = 0u;
+    int row = i;
+    for (int m = 0; m < C && row < k; ++m, row += L) {
+      const uint32_t v = src[(size_t)row * ld + col];
+      acc = m == 0 ? v : m_add(acc, m_rot_rt(v, (uint32_t)(eC * m * cc)));
+    }
+    if (cc != 0) acc = m_mul(acc, __ldg(powf + ((i * cc) & nmask)));
+    return acc;
+  }
+};
+
+// Rows [row0, row0 + L) of a u32 matrix (row0 = blockIdx.y * L).
+template <int WT>
+struct LoadRows32 {
+  const uint32_t* in;
+  size_t ld;
+  size_t row0;
+  int col0, W;
+  uint32_t rmul, nmask;
+  static __device__ __forceinline__ LoadRows32 make(const KArgs& a) {
+    return LoadRows32{static_cast<const uint32_t*>(a.in), a.ld_in, (size_t)blockIdx.y * a.L,
+                      (int)blockIdx.x * WT, a.W, a.in_row_mul, (uint32_t)a.n - 1u};
+  }
+  __device__ __forceinline__ uint32_t operator()(int i, int c) const {
+    const int col = col0 + c;
+    if (col >= W) return 0u;
+    size_t row = row0 + i;
+    if (rmul != 1u) row = (rmul * (uint32_t)row) & nmask;
+    return in[row * ld + col];
+  }
+};
+
+// Decode step 4 + the scatter of step 5 (Sec. II.B): the length-n vector
+// u[z] = v_i * c_i at z = z_i (the first k received positions), 0 elsewhere,
+// with c_i = -r^(-z_i) / A'(r^(z_i)) from the pattern table.
+template <int WT>
+struct LoadRecv {
+  const uint32_t* recv;
+  size_t ld;
+  const uint2* pat;
+  int* status;
+  size_t z0;
+  int col0, W, slots;
+  static __device__ __forceinline__ LoadRecv make(const KArgs& a) {
+    return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status, 0,
+                    (int)blockIdx.x * WT, a.W, a.slots};
+  }
+  __device__ __forceinline__ uint32_t operator()(int i, int c) const {
+    const int col = col0 + c;
+    if (col >= W) return 0u;
+    const uint2 e = __ldg(pat + z0 + i);
+    if ((int)e.x < 0) return 0u;
+    const size_t row = slots ? (size_t)(z0 + i) : (size_t)e.x;
+    const uint32_t v = recv[row * ld + col];
+    if (v > 65536u) atomicOr(status, ST_RANGE);
+    return m_mul(v, e.y);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Storers: spectrum index j of tile codeword c.
+// ---------------------------------------------------------------------------
+
+// out row = cc + C*j, value reduced to [0, p) and optionally scaled.
+template <int WT>
+struct StoreRows32 {
+  uint32_t* out;
+  size_t ld;
+  int col0, W, C, cc;
+  uint32_t scale, rmul, nmask;
+  static __device__ __forceinline__ StoreRows32 make(const KArgs& a) {
+    return StoreRows32{static_cast<uint32_t*>(a.out), a.ld_out, (int)blockIdx.x * WT, a.W, a.C,
+                       (int)blockIdx.y, a.scale, a.row_mul, (uint32_t)a.n - 1u};
+  }
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
+    const int col = col0 + c;
+    if (col >= W) return;
+    if (scale != 1u) v = m_mul(v, scale);
+    uint32_t row = (uint32_t)(cc + C * j);
+    if (rmul != 1u) row = (rmul * row) & nmask;
+    out[(size_t)row * ld + col] = m_to_p(v);
+  }
+};
+
+__device__ __forceinline__ uint16_t to_symbol(uint32_t v, int* status) {
+  const uint32_t r = m_to_p(v);
+  if (r == 65536u) {
+    atomicOr(status, ST_RANGE);
+    return 0;
+  }
+  return (uint16_t)r;
+}
+
+// Local pass of a split transform (n = C * L): spectrum index j of block j1
+// is row j1 + C*j of the full transform.
+template <int WT, int MODE>
+struct StoreLocal {
+  KArgs a;
+  int col0, j1;
+  static __device__ __forceinline__ StoreLocal make(const KArgs& a) {
+    return StoreLocal{a, (int)blockIdx.x * WT, (int)blockIdx.y};
+  }
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
+    const int col = col0 + c;
+    if (col >= a.W) return;
+    const size_t row = (size_t)j1 + (size_t)a.C * j;
+    if constexpr (MODE == LM_ENC || MODE == LM_FNT) {
+      if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
+      const size_t orow = a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
+      static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
+    } else if constexpr (MODE == LM_WORK) {
+      if ((int)row < a.out_limit) static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
+    } else if constexpr (MODE == LM_WORK_AHAT) {
+      static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(v, __ldg(a.ahat + row));
+    } else if constexpr (MODE == LM_OUT16) {
+      if ((int)row < a.out_limit)
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, a.status);
+    } else if constexpr (MODE == LM_SPLIT) {
+      if ((int)row < a.h)
+        static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
+      else if ((int)row < a.out_limit)
+        static_cast<uint32_t*>(a.out3)[(row - a.h) * a.ld_work + col] = v;
+    } else if constexpr (MODE == LM_X_PARTIAL) {
+      const uint32_t vp = m_to_p(v);
+      static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(vp, __ldg(a.ahat + row));
+      static_cast<uint32_t*>(a.out3)[row * a.ld_work + col] = m_mul(vp, __ldg(a.ahat2 + row));
+    } else if constexpr (MODE == LM_ACCUM) {
+      uint32_t* p = static_cast<uint32_t*>(a.out3) + row * a.ld_work + col;
+      *p = m_add(*p, m_mul(v, __ldg(a.ahat + row)));
+    } else if constexpr (MODE == LM_OUT16_ADD) {
+      if ((int)row < a.out_limit) {
+        if ((int)row >= a.h)
+          v = m_add(v, static_cast<const uint32_t*>(a.in2)[(row - a.h) * a.ld_work + col]);
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, a.status);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Generic tile transform: DIF passes from a loader to a storer.
+// grid = (ceil(W / WT), classes or blocks), dynamic smem = L * WT * 4 bytes.
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT, bool INV, class LD, class ST>
+__global__ void __launch_bounds__(NT) k_tile(KArgs a) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  LD load = LD::make(a);
+  ST store = ST::make(a);
+  const uint32_t* tw = INV ? a.twi : a.twf;
+  dif_first<S, WT, NT, INV>(sm, tw, load, store);
+  if constexpr (S::NP >= 2) {
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, WT, NT, INV>(sm, tw + S::TW2_OFF);
+      __syncthreads();
+    }
+    dif_last<S, WT, NT, INV>(sm, store);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cross pass of a split transform n = C * L (C <= 16): for every i2 < L and
+// column, the radix-C DFT over rows i1*L + i2 followed by the twiddle
+// r_n^(+-i2*j1); result row j1*L + i2 of the workspace matrix out2.
+// ---------------------------------------------------------------------------
+template <int C, bool INV, int LOADM>
+__global__ void __launch_bounds__(256) k_cross(KArgs a) {
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  const int col = (int)(t % a.W);
+  const long long i2l = t / a.W;
+  if (i2l >= a.L) return;
+  const int i2 = (int)i2l;
+  uint32_t x[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const int row = q * a.L + i2;
+    if constexpr (LOADM == CL_SRC16) {
+      x[q] = row < a.row_limit ? (uint32_t)static_cast<const uint16_t*>(a.in)[(size_t)row * a.ld_in + col]
+                               : 0u;
+    } else if constexpr (LOADM == CL_U32) {
+      const uint32_t r = a.in_row_mul == 1u ? (uint32_t)row
+                                            : ((a.in_row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
+      x[q] = row < a.row_limit ? static_cast<const uint32_t*>(a.in)[(size_t)r * a.ld_in + col]
+                               : 0u;
+    } else {
+      const uint2 e = __ldg(a.pat + row);
+      uint32_t v = 0u;
+      if ((int)e.x >= 0) {
+        const size_t rr = a.slots ? (size_t)row : (size_t)e.x;
+        v = static_cast<const uint32_t*>(a.in)[rr * a.ld_in + col];
+        if (v > 65536u) atomicOr(a.status, ST_RANGE);
+        v = m_mul(v, e.y);
+      }
+      x[q] = v;
+    }
+  }
+  dft_reg<C, INV>(x);
+  const uint32_t* pw = INV ? a.powi : a.powf;
+  constexpr int B = ilog2(C);
+  uint32_t* out = static_cast<uint32_t*>(a.out2);
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const int j1 = bitrev(q, B);
+    uint32_t v = x[q];
+    if (j1 != 0) v = m_mul(v, __ldg(pw + (((long long)i2 * j1) & (a.n - 1))));
+    out[((size_t)j1 * a.L + i2) * a.ld_work + col] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused decode for n = L <= tile limit and k <= n/2 (Sec. II.B steps 4-6):
+//   T = FNT_n with root r^-1 of u (DIF, slots),  S_j = T_j for j < k,
+//   F = FNT_n(S) (DIT, natural),  G = F * ahat  (ahat = n^-1 FNT_n(A mod x^k)),
+//   P = FNT_n with root r^-1 of G (DIF), out_j = P_j for j < k.
+// The boundary passes of consecutive transforms act on the same register
+// groups and are fused.
+// ---------------------------------------------------------------------------
+template <int WT>
+struct StoreOut16 {
+  uint16_t* out;
+  size_t ld;
+  int* status;
+  int col0, W, k;
+  static __device__ __forceinline__ StoreOut16 make(const KArgs& a) {
+    return StoreOut16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, (int)blockIdx.x * WT,
+                      a.W, a.k};
+  }
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
+    const int col = col0 + c;
+    if (col >= W || j >= k) return;
+    out[(size_t)j * ld + col] = to_symbol(v, status);
+  }
+};
+
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT) k_decode(KArgs a) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  LoadRecv<WT> load = LoadRecv<WT>::make(a);
+  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  const uint32_t* __restrict__ ahat = a.ahat;
+  if constexpr (S::NP == 1) {
+    constexpr int R = S::L, B = ilog2(R);
+    for (int c = threadIdx.x; c < WT; c += NT) {
+      uint32_t x[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) x[i] = load(i, c);
+      dft_reg<R, true>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (bitrev(q, B) >= a.k) x[q] = 0u;
+      bitrev_regs<R>(x);
+      dft_reg<R, false>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B)));
+      bitrev_regs<R>(x);
+      dft_reg<R, true>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q) store(bitrev(q, B), c, x[q]);
+    }
+  } else {
+    const uint32_t* tw1f = a.twf;
+    const uint32_t* tw1i = a.twi;
+    // D1 passes (root r^-1), natural -> slots
+    {
+      struct Nop {
+        __device__ void operator()(int, int, uint32_t) const {}
+      } nop;
+      dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
+    }
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+      __syncthreads();
+    }
+    // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
+    {
+      constexpr int R = S::RL, B = ilog2(R);
+      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+        const int c = t % WT, b = t / WT;
+        uint32_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+        dft_reg<R, true>(x);
+        const int base = S::natural(b * R);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (base + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
+        bitrev_regs<R>(x);
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
+      }
+    }
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
+      __syncthreads();
+    }
+    // last D2 pass (DIT, natural output) * ahat + first D3 pass (DIF, root r^-1)
+    {
+      constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+        const int c = t % WT, i2 = t / WT;
+        uint32_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+        twiddle_regs<R>(x, tw1f + i2 * R);
+        bitrev_regs<R>(x);
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
+        bitrev_regs<R>(x);
+        dft_reg<R, true>(x);
+        twiddle_regs<R>(x, tw1i + i2 * R);
+#pragma unroll
+        for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
+      }
+    }
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+      __syncthreads();
+    }
+    dif_last<S, WT, NT, true>(sm, store);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused decode for n = L and k > n/2: the truncated product of step 6 is
+// split at h = n/2 so that only length-n cyclic products occur:
+//   P mod x^k = A0 S0 + x^h (A0 S1 + A1 S0),  A = A0 + x^h A1, S = S0 + x^h S1.
+// Buffers X (S0 path) and Y (S1 path) in shared memory; ahat = n^-1 FNT(A0),
+// ahat2 = n^-1 FNT(A1).  Output P_j = X_j + (j >= h ? Y_(j-h) : 0).
+// ---------------------------------------------------------------------------
+// One codeword per thread, everything in registers (L <= 32).
+template <int L, int WT, int NT>
+__device__ __forceinline__ void decode_split_regs(const KArgs& a) {
+  constexpr int B = ilog2(L), H = L / 2;
+  LoadRecv<WT> load = LoadRecv<WT>::make(a);
+  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  for (int c = threadIdx.x; c < WT; c += NT) {
+    uint32_t x[L], y[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) x[i] = load(i, c);
+    dft_reg<L, true>(x);
+    bitrev_regs<L>(x);  // x[j] = T_j
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      y[j] = (H + j < a.k) ? x[H + j] : 0u;
+      y[j + H] = 0u;
+      x[j + H] = 0u;
+    }
+    dft_reg<L, false>(x);
+    dft_reg<L, false>(y);
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      const int i = bitrev(q, B);
+      const uint32_t a0 = __ldg(a.ahat + i), a1 = __ldg(a.ahat2 + i);
+      const uint32_t s0 = m_to_p(x[q]);
+      x[q] = m_mul(s0, a0);
+      y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
+    }
+    bitrev_regs<L>(x);
+    bitrev_regs<L>(y);
+    dft_reg<L, true>(x);
+    dft_reg<L, true>(y);
+    bitrev_regs<L>(x);
+    bitrev_regs<L>(y);
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      uint32_t v = x[j];
+      if (j >= H) v = m_add(v, y[j - H]);
+      store(j, c, v);
+    }
+  }
+}
+
+template <class S, int WT, int NT>
+__device__ __forceinline__ void decode_split_smem(const KArgs& a) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* Y = X + S::L * WT;
+  LoadRecv<WT> load = LoadRecv<WT>::make(a);
+  const uint32_t* tw1f = a.twf;
+  const uint32_t* tw1i = a.twi;
+  const int k = a.k, h = S::L / 2;
+  {
+    struct Nop {
+      __device__ void operator()(int, int, uint32_t) const {}
+    } nop;
+    dif_first<S, WT, NT, true>(X, tw1i, load, nop);
+  }
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, WT, NT, true>(X, tw1i + S::TW2_OFF);
+    __syncthreads();
+  }
+  // last D1 pass; split T_j (j < k) into S0 (j < h) and S1 (h <= j < k)
+  {
+    constexpr int R = S::RL, B = ilog2(R), HR = R / 2;
+    for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+      const int c = t % WT, b = t / WT;
+      uint32_t x[R], y[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = X[sm_addr<S, WT>(b * R + q, c)];
+      dft_reg<R, true>(x);
+      bitrev_regs<R>(x);  // x[d] = digit d
+      const int base = S::natural(b * R);
+#pragma unroll
+      for (int d = 0; d < HR; ++d) {
+        y[d] = (base + (S::L / R) * (d + HR) < k) ? x[d + HR] : 0u;
+        y[d + HR] = 0u;
+        x[d + HR] = 0u;
+      }
+      dft_reg<R, false>(x);
+      dft_reg<R, false>(y);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        X[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
+        Y[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = y[q];
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dit_mid<S, WT, NT, false>(X, tw1f + S::TW2_OFF);
+    dit_mid<S, WT, NT, false>(Y, tw1f + S::TW2_OFF);
+    __syncthreads();
+  }
+  // last D2 pass on both, Xf = S0^ A0^, Yf = S1^ A0^ + S0^ A1^, first D3 pass on both
+  {
+    constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+    for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+      const int c = t % WT, i2 = t / WT;
+      uint32_t x[R], y[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        x[q] = X[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+        y[q] = Y[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+      }
+      twiddle_regs<R>(x, tw1f + i2 * R);
+      twiddle_regs<R>(y, tw1f + i2 * R);
+      bitrev_regs<R>(x);
+      bitrev_regs<R>(y);
+      dft_reg<R, false>(x);
+      dft_reg<R, false>(y);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = bitrev(q, B) * SP + i2;
+        const uint32_t a0 = __ldg(a.ahat + i), a1 = __ldg(a.ahat2 + i);
+        const uint32_t s0 = m_to_p(x[q]);
+        x[q] = m_mul(s0, a0);
+        y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
+      }
+      bitrev_regs<R>(x);
+      bitrev_regs<R>(y);
+      dft_reg<R, true>(x);
+      dft_reg<R, true>(y);
+      twiddle_regs<R>(x, tw1i + i2 * R);
+      twiddle_regs<R>(y, tw1i + i2 * R);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        X[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
+        Y[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = y[q];
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, WT, NT, true>(X, tw1i + S::TW2_OFF);
+    dif_mid<S, WT, NT, true>(Y, tw1i + S::TW2_OFF);
+    __syncthreads();
+  }
+  // last D3 pass on both; P_j = X_j + (j >= h ? Y_(j-h) : 0)
+  {
+    constexpr int R = S::RL, HR = R / 2;
+    uint16_t* out = static_cast<uint16_t*>(a.out);
+    const int col0 = blockIdx.x * WT;
+    for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+      const int c = t % WT, b = t / WT;
+      const int col = col0 + c;
+      uint32_t x[R], y[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        x[q] = X[sm_addr<S, WT>(b * R + q, c)];
+        y[q] = Y[sm_addr<S, WT>(b * R + q, c)];
+      }
+      dft_reg<R, true>(x);
+      dft_reg<R, true>(y);
+      bitrev_regs<R>(x);
+      bitrev_regs<R>(y);
+      const int base = S::natural(b * R);
+      if (col < a.W) {
+#pragma unroll
+        for (int d = 0; d < R; ++d) {
+          const int j = base + (S::L / R) * d;
+          uint32_t v = x[d];
+          if (d >= HR) v = m_add(v, y[d - HR]);
+          if (j < k) out[(size_t)j * a.ld_out + col] = to_symbol(v, a.status);
+        }
+      }
+    }
+  }
+  (void)h;
+}
+
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
+  if constexpr (S::NP == 1) {
+    decode_split_regs<S::L, WT, NT>(a);
+  } else {
+    decode_split_smem<S, WT, NT>(a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One level of the product tree for A(x) = prod (x - x_i) (step 1 of
+// Sec. II.B, divide and conquer with FNT products, "M(n) = 3 FNTs"):
+// child nodes of degree <= d are multiplied in pairs with a cyclic product of
+// length L = 2d.  Level matrices are [d+1][nodes] (column = node).  Both
+// children full (degree d) means the product has degree 2d = L: its leading
+// 1 wraps onto coefficient 0 and is moved back.
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT) k_poly_level(KArgs a) {
+  static_assert(S::NP >= 2, "");
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* Y = X + S::L * WT;
+  const uint32_t* lvl = static_cast<const uint32_t*>(a.in);
+  const size_t ldl = a.ld_in;  // = nodes
+  const int d = a.deg_child, nodes = a.nodes, k = a.k;
+  const int p0 = blockIdx.x * WT;
+  struct LoadChild {
+    const uint32_t* lvl;
+    size_t ld;
+    int d, nodes, p0, side;
+    __device__ uint32_t operator()(int i, int c) const {
+      const int node = 2 * (p0 + c) + side;
+      if (node >= nodes) return (side == 1 && i == 0 && 2 * (p0 + c) < nodes) ? 1u : 0u;
+      return i <= d ? lvl[(size_t)i * ld + node] : 0u;
+    }
+  };
+  struct Nop {
+    __device__ void operator()(int, int, uint32_t) const {}
+  } nop;
+  const uint32_t* twf = a.twf;
+  const uint32_t* twi = a.twi;
+  LoadChild la{lvl, ldl, d, nodes, p0, 0}, lb{lvl, ldl, d, nodes, p0, 1};
+  dif_first<S, WT, NT, false>(X, twf, la, nop);
+  dif_first<S, WT, NT, false>(Y, twf, lb, nop);
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, WT, NT, false>(X, twf + S::TW2_OFF);
+    dif_mid<S, WT, NT, false>(Y, twf + S::TW2_OFF);
+    __syncthreads();
+  }
+  dif_last_inplace<S, WT, NT, false>(X);
+  dif_last_inplace<S, WT, NT, false>(Y);
+  __syncthreads();
+  dit_last_inplace<S, WT, NT, true, true>(X, Y);
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dit_mid<S, WT, NT, true>(X, twi + S::TW2_OFF);
+    __syncthreads();
+  }
+  struct StoreProd {
+    uint32_t* out;
+    size_t ld;
+    int d, k, p0, npairs;
+    uint32_t linv;
+    __device__ void operator()(int i, int c, uint32_t v) const {
+      const int p = p0 + c;
+      if (p >= npairs) return;
+      // product degree == 2d only if both children are full
+      const bool full = (long long)k >= (long long)(2 * p + 2) * d;
+      uint32_t r = m_to_p(m_mul(v, linv));
+      if (i == 0 && full) r = r == 0u ? 65536u : r - 1u;
+      out[(size_t)i * ld + p] = r;
+      if (i == 0) out[(size_t)(2 * d) * ld + p] = full ? 1u : 0u;
+    }
+  };
+  const int npairs = (nodes + 1) / 2;
+  StoreProd sp{static_cast<uint32_t*>(a.out), (size_t)npairs, d, k, p0, npairs, a.scale};
+  dit_first<S, WT, NT, true>(X, twi, sp);
+}
+
+}  // namespace fntrs

@@ -1,0 +1,795 @@
+// Host side of libfntrs: plans, twiddle tables, pattern cache, dispatch and
+// the C ABI declared in include/fnt_rs.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/fnt_rs.h"
+#include "kargs.h"
+#include "sched.h"
+
+namespace fntrs {
+
+// ---------------------------------------------------------------------------
+// launch counter and tile-op registry
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static TileOps g_ops[17];
+static std::once_flag g_ops_once;
+
+void register_ops(const TileOps& ops) {
+  int b = 0;
+  while ((1 << b) < ops.L) ++b;
+  g_ops[b] = ops;
+}
+
+static void init_ops() {
+  std::call_once(g_ops_once, [] {
+    register_tile_ops_small();
+    register_tile_ops_mid();
+    register_tile_ops_big();
+  });
+}
+
+const TileOps& tile_ops(int L) {
+  init_ops();
+  int b = 0;
+  while ((1 << b) < L) ++b;
+  return g_ops[b];
+}
+
+void launch_pat_init(uint2* pat, int n, cudaStream_t st);
+void launch_leaves(const uint32_t* pos, int k, const uint32_t* powf, uint32_t* out, int nodes,
+                   cudaStream_t st);
+void launch_big_pack(const uint32_t* lvl, int d, int nodes, int L, uint32_t* M, cudaStream_t st);
+void launch_big_mul(const uint32_t* Mh, int npairs, int L, uint32_t* Q, cudaStream_t st);
+void launch_big_fix(const uint32_t* Q, int d, int k, int npairs, int L, uint32_t* out,
+                    cudaStream_t st);
+void launch_pat_prep(const uint32_t* A, int k, int n, int ncols, int h, uint32_t* M,
+                     cudaStream_t st);
+void launch_pat_final(const uint32_t* E, int ncols, const uint32_t* pos, int k, int n,
+                      const uint32_t* powi, uint32_t ninv, uint2* pat, uint32_t* ahat,
+                      uint32_t* ahat2, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// F_p helpers on the host (plan tables)
+// ---------------------------------------------------------------------------
+static uint32_t hmul(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) % FNT_RS_P); }
+static uint32_t hpow(uint32_t a, uint64_t e) {
+  uint64_t r = 1, b = a % FNT_RS_P;
+  while (e) {
+    if (e & 1) r = r * b % FNT_RS_P;
+    b = b * b % FNT_RS_P;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+static uint32_t hinv(uint32_t a) { return hpow(a, FNT_RS_P - 2); }
+static int ilog2i(uint32_t v) {
+  int b = 0;
+  while ((1u << b) < v) ++b;
+  return b;
+}
+static int bitrev_h(int v, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+// default root of order n: 3^(65536/n) (Sec. II.B)
+static uint32_t default_root(uint32_t n) { return hpow(3, 65536u / n); }
+
+// ---------------------------------------------------------------------------
+// Device tables per transform length L (default root), shared by all plans
+// on a device: per-pass schedule tables and the powers r_L^e, r_L^-e.
+// ---------------------------------------------------------------------------
+struct Tables {
+  uint32_t* twf = nullptr;
+  uint32_t* twi = nullptr;
+  uint32_t* powf = nullptr;
+  uint32_t* powi = nullptr;
+};
+
+static std::mutex g_tab_mu;
+static std::map<std::pair<int, int>, Tables> g_tables;
+
+static std::vector<uint32_t> sched_table(int L, bool inverse) {
+  int r[3];
+  sched_radices(L, r);
+  std::vector<uint32_t> out;
+  if (r[1] == 1) return out;  // single pass: no twiddles
+  uint32_t w = default_root(L);
+  if (inverse) w = hinv(w);
+  const int S1 = L / r[0];
+  out.resize(L + (r[2] > 1 ? S1 : 0));
+  const int b0 = ilog2i(r[0]);
+  for (int i2 = 0; i2 < S1; ++i2)
+    for (int q = 0; q < r[0]; ++q)
+      out[(size_t)i2 * r[0] + q] = hpow(w, (uint64_t)i2 * bitrev_h(q, b0) % L);
+  if (r[2] > 1) {
+    const uint32_t w2 = hpow(w, r[0]);  // root of order S1
+    const int S2 = S1 / r[1], b1 = ilog2i(r[1]);
+    for (int i2 = 0; i2 < S2; ++i2)
+      for (int q = 0; q < r[1]; ++q)
+        out[L + (size_t)i2 * r[1] + q] = hpow(w2, (uint64_t)i2 * bitrev_h(q, b1) % S1);
+  }
+  return out;
+}
+
+static int upload(uint32_t** dst, const std::vector<uint32_t>& v) {
+  const size_t bytes = std::max<size_t>(16, v.size() * sizeof(uint32_t));
+  if (cudaMalloc(dst, bytes) != cudaSuccess) return FNT_RS_E_CUDA;
+  if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return FNT_RS_E_CUDA;
+  return FNT_RS_OK;
+}
+
+static int get_tables(int L, Tables* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FNT_RS_E_CUDA;
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  auto it = g_tables.find({dev, L});
+  if (it != g_tables.end()) {
+    *out = it->second;
+    return FNT_RS_OK;
+  }
+  Tables t;
+  std::vector<uint32_t> pf(L), pi(L);
+  const uint32_t r = default_root(L), ri = hinv(r);
+  uint32_t a = 1, b = 1;
+  for (int e = 0; e < L; ++e) {
+    pf[e] = a;
+    pi[e] = b;
+    a = hmul(a, r);
+    b = hmul(b, ri);
+  }
+  int rc;
+  if ((rc = upload(&t.powf, pf)) || (rc = upload(&t.powi, pi))) return rc;
+  if (L <= kTileMaxL) {
+    if ((rc = upload(&t.twf, sched_table(L, false))) || (rc = upload(&t.twi, sched_table(L, true))))
+      return rc;
+  }
+  g_tables[{dev, L}] = t;
+  *out = t;
+  return FNT_RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct PatternSlot {
+  std::vector<uint32_t> key;
+  uint64_t last_use = 0;
+  bool valid = false;
+  uint2* pat = nullptr;
+  uint32_t* ahat = nullptr;
+  uint32_t* ahat2 = nullptr;
+  uint32_t* pos_d = nullptr;  // first k positions (device)
+  uint32_t* pos_h = nullptr;  // pinned staging of the upload
+  cudaEvent_t staged = nullptr;  // recorded after the upload
+};
+
+constexpr int kPatternSlots = 4;
+constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
+
+}  // namespace fntrs
+
+using namespace fntrs;
+
+struct fnt_rs_plan_s {
+  int dev = 0;
+  uint32_t n = 0, k = 0, root = 0;
+  uint32_t u = 1, uinv = 1;  // root = default^u; spectrum index j -> row uinv*j
+  uint32_t ninv = 1;
+  bool split = false;  // n > tile limit: n = C * kLocalL
+  int C = 1;
+  bool blocked = false;  // k > n/2
+  Tables tn;             // tables of length n (pow tables; schedule tables if n <= tile)
+  Tables tl;             // tables of the local length (split only)
+  int* status = nullptr;
+  uint32_t* pscratch = nullptr;
+  size_t pscratch_words = 0;
+  PatternSlot slots[kPatternSlots];
+  int current = -1;
+  uint64_t clock = 0;
+};
+
+namespace fntrs {
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? FNT_RS_OK : FNT_RS_E_CUDA; }
+
+// columns per chunk of a split transform with `nbuf` [n][Wc] workspace buffers
+static size_t split_chunk(uint32_t n, int nbuf) {
+  size_t wc = kChunkBudget / ((size_t)nbuf * n * 4);
+  wc = std::max<size_t>(8, wc / 8 * 8);
+  return wc;
+}
+
+static int enc_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+static int dec_nbuf(const fnt_rs_plan_s* p) { return p->split ? (p->blocked ? 4 : 2) : 0; }
+static int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+
+static size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf) {
+  if (nbuf == 0 || W == 0) return 0;
+  const size_t wc = std::min(W, split_chunk(p->n, nbuf));
+  return (size_t)nbuf * p->n * wc * 4;
+}
+
+// Batched transform of an [L][W] u32 matrix with the default root of order L,
+// out = (inverse ? L^-1 : 1) * scale_extra * FNT(in), values reduced.
+// For L above the tile limit the caller provides `work` of L*W words.
+static int run_fnt_default(int L, const uint32_t* in, size_t ld_in, uint32_t* out, size_t ld_out,
+                           int W, bool inverse, uint32_t row_mul, uint32_t* work,
+                           cudaStream_t st) {
+  Tables t;
+  int rc = get_tables(L, &t);
+  if (rc) return rc;
+  const uint32_t scale = inverse ? hinv((uint32_t)L % FNT_RS_P) : 1u;
+  if (L <= kTileMaxL) {
+    const TileOps& ops = tile_ops(L);
+    KArgs a;
+    a.in = in;
+    a.ld_in = ld_in;
+    a.out = out;
+    a.ld_out = ld_out;
+    a.W = W;
+    a.n = L;
+    a.L = L;
+    a.C = 1;
+    a.scale = scale;
+    a.twf = t.twf;
+    a.twi = t.twi;
+    (inverse ? a.in_row_mul : a.row_mul) = row_mul;
+    (inverse ? ops.fnt_inv : ops.fnt_fwd)(a, 1, st);
+    return cuda_ok(cudaGetLastError());
+  }
+  Tables tl;
+  if ((rc = get_tables(kLocalL, &tl))) return rc;
+  const int C = L / kLocalL;
+  KArgs a;
+  a.in = in;
+  a.ld_in = ld_in;
+  a.out = out;
+  a.ld_out = ld_out;
+  a.out2 = work;
+  a.ld_work = (size_t)W;
+  a.W = W;
+  a.n = L;
+  a.L = kLocalL;
+  a.C = C;
+  a.row_limit = L;
+  a.scale = scale;
+  a.powf = t.powf;
+  a.powi = t.powi;
+  (inverse ? a.in_row_mul : a.row_mul) = row_mul;
+  cross_launcher(C, inverse, CL_U32)(a, 1, st);
+  KArgs b = a;
+  b.in = work;
+  b.ld_in = (size_t)W;
+  b.twf = tl.twf;
+  b.twi = tl.twi;
+  local_launcher(inverse, LM_FNT)(b, C, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// pattern build (steps 1-3) into slot `si`
+// ---------------------------------------------------------------------------
+static size_t pattern_scratch_words(uint32_t n, uint32_t k) {
+  // level ping-pong, [n][3] matrix + transform, big-level matrices + work
+  size_t K2 = 1;
+  while (K2 < k) K2 <<= 1;
+  const size_t lvl = 4 * (size_t)k + 4 * 64 + 2 * K2 + 64;
+  const size_t big = (K2 > (size_t)kTileMaxL / 2) ? 8 * (size_t)(2 * K2) + 8 * K2 : 0;
+  return 2 * lvl + 9 * (size_t)n + big + 1024;
+}
+
+static int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
+  const int n = (int)p->n, k = (int)p->k;
+  uint32_t* base = p->pscratch;
+  size_t K2 = 1;
+  while (K2 < (size_t)k) K2 <<= 1;
+  const size_t lvl_words = 4 * (size_t)k + 4 * 64 + 2 * K2 + 64;
+  uint32_t* lv[2] = {base, base + lvl_words};
+  uint32_t* M = base + 2 * lvl_words;
+  uint32_t* E = M + 3 * (size_t)n;
+  uint32_t* work = E + 3 * (size_t)n;        // 3n words: split-transform work of the pattern FNT
+  uint32_t* big = work + 3 * (size_t)n;       // big-level matrices
+  int rc;
+  launch_pat_init(sl.pat, n, st);
+  // step 1: leaves (up to 32 factors per node) then pairwise FNT products
+  int nodes = (k + 31) / 32, d = 32;
+  launch_leaves(sl.pos_d, k, p->tn.powf, lv[0], nodes, st);
+  int cur = 0;
+  while (nodes > 1) {
+    const int L = 2 * d, npairs = (nodes + 1) / 2;
+    uint32_t* dst = lv[cur ^ 1];
+    if (L <= kTileMaxL) {
+      Tables t;
+      if ((rc = get_tables(L, &t))) return rc;
+      KArgs a;
+      a.in = lv[cur];
+      a.ld_in = (size_t)nodes;
+      a.out = dst;
+      a.k = k;
+      a.L = L;
+      a.deg_child = d;
+      a.nodes = nodes;
+      a.twf = t.twf;
+      a.twi = t.twi;
+      a.scale = hinv((uint32_t)L % FNT_RS_P);
+      tile_ops(L).poly_level(a, 1, st);
+    } else {
+      const int cols = 2 * npairs;
+      uint32_t* Mb = big;
+      uint32_t* Mh = Mb + (size_t)L * cols;
+      uint32_t* Q = Mh + (size_t)L * cols;
+      uint32_t* Qi = Q + (size_t)L * npairs;
+      uint32_t* wk = Qi + (size_t)L * npairs;
+      launch_big_pack(lv[cur], d, nodes, L, Mb, st);
+      if ((rc = run_fnt_default(L, Mb, cols, Mh, cols, cols, false, 1, wk, st))) return rc;
+      launch_big_mul(Mh, npairs, L, Q, st);
+      if ((rc = run_fnt_default(L, Q, npairs, Qi, npairs, npairs, true, 1, wk, st))) return rc;
+      launch_big_fix(Qi, d, k, npairs, L, dst, st);
+    }
+    cur ^= 1;
+    nodes = npairs;
+    d = L;
+  }
+  // steps 2-3 and the step-6 transform(s)
+  const int ncols = p->blocked ? 3 : 2;
+  launch_pat_prep(lv[cur], k, n, ncols, n / 2, M, st);
+  if ((rc = run_fnt_default(n, M, ncols, E, ncols, ncols, false, 1, work, st))) return rc;
+  launch_pat_final(E, ncols, sl.pos_d, k, n, p->tn.powi, p->ninv, sl.pat, sl.ahat, sl.ahat2, st);
+  return cuda_ok(cudaGetLastError());
+}
+
+static int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos) {
+  if (!pos) return FNT_RS_E_ARG;
+  if (npos < p->k) return FNT_RS_E_POSITIONS;
+  std::vector<uint8_t> seen(p->n, 0);
+  for (uint32_t i = 0; i < npos; ++i) {
+    if (pos[i] >= p->n || seen[pos[i]]) return FNT_RS_E_POSITIONS;
+    seen[pos[i]] = 1;
+  }
+  return FNT_RS_OK;
+}
+
+// Find or build the pattern of the first k positions; sets p->current.
+static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, cudaStream_t st) {
+  int rc = validate_positions(p, positions, npos);
+  if (rc) return rc;
+  // map positions for a non-default root: r'^z = r^(u z)
+  std::vector<uint32_t> key(positions, positions + p->k);
+  if (p->u != 1)
+    for (auto& z : key) z = (uint32_t)(((uint64_t)z * p->u) & (p->n - 1));
+  ++p->clock;
+  for (int s = 0; s < kPatternSlots; ++s) {
+    if (p->slots[s].valid && p->slots[s].key == key) {
+      p->slots[s].last_use = p->clock;
+      p->current = s;
+      return FNT_RS_OK;
+    }
+  }
+  int victim = 0;
+  for (int s = 0; s < kPatternSlots; ++s) {
+    if (!p->slots[s].valid) { victim = s; break; }
+    if (p->slots[s].last_use < p->slots[victim].last_use) victim = s;
+  }
+  PatternSlot& sl = p->slots[victim];
+  sl.valid = false;
+  // the slot's staging buffer may still feed its previous upload
+  if ((rc = cuda_ok(cudaEventSynchronize(sl.staged)))) return rc;
+  std::memcpy(sl.pos_h, key.data(), key.size() * 4);
+  if ((rc = cuda_ok(cudaMemcpyAsync(sl.pos_d, sl.pos_h, key.size() * 4, cudaMemcpyHostToDevice, st))))
+    return rc;
+  if ((rc = cuda_ok(cudaEventRecord(sl.staged, st)))) return rc;
+  if ((rc = build_pattern(p, sl, st))) return rc;
+  sl.key.swap(key);
+  sl.valid = true;
+  sl.last_use = p->clock;
+  p->current = victim;
+  return FNT_RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// encode / decode / fnt dispatch
+// ---------------------------------------------------------------------------
+static int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                     size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
+  if (!p->split) {
+    const TileOps& ops = tile_ops((int)p->n);
+    KArgs a;
+    a.in = src;
+    a.ld_in = ld_src;
+    a.out = enc;
+    a.ld_out = ld_enc;
+    a.W = (int)W;
+    a.n = (int)p->n;
+    a.k = (int)p->k;
+    a.L = (int)p->n;
+    a.C = 1;
+    a.twf = p->tn.twf;
+    a.twi = p->tn.twi;
+    a.powf = p->tn.powf;
+    a.row_mul = p->uinv;
+    ops.encode(a, 1, st);
+    return cuda_ok(cudaGetLastError());
+  }
+  const size_t wc = split_chunk(p->n, 1);
+  uint32_t* work = static_cast<uint32_t*>(workspace);
+  for (size_t c0 = 0; c0 < W; c0 += wc) {
+    const int w = (int)std::min(wc, W - c0);
+    KArgs a;
+    a.in = src + c0;
+    a.ld_in = ld_src;
+    a.out = enc + c0;
+    a.ld_out = ld_enc;
+    a.out2 = work;
+    a.ld_work = (size_t)w;
+    a.W = w;
+    a.n = (int)p->n;
+    a.k = (int)p->k;
+    a.L = kLocalL;
+    a.C = p->C;
+    a.row_limit = (int)p->k;
+    a.powf = p->tn.powf;
+    a.powi = p->tn.powi;
+    a.row_mul = p->uinv;
+    cross_launcher(p->C, false, CL_SRC16)(a, 1, st);
+    KArgs b = a;
+    b.in = work;
+    b.ld_in = (size_t)w;
+    b.twf = p->tl.twf;
+    b.twi = p->tl.twi;
+    local_launcher(false, LM_ENC)(b, p->C, st);
+  }
+  return cuda_ok(cudaGetLastError());
+}
+
+static int do_decode(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, uint16_t* out,
+                     size_t ld_out, size_t W, void* workspace, cudaStream_t st, int slots) {
+  const PatternSlot& sl = p->slots[p->current];
+  KArgs a;
+  a.slots = slots;
+  a.in = recv;
+  a.ld_in = ld_recv;
+  a.out = out;
+  a.ld_out = ld_out;
+  a.n = (int)p->n;
+  a.k = (int)p->k;
+  a.h = (int)p->n / 2;
+  a.pat = sl.pat;
+  a.ahat = sl.ahat;
+  a.ahat2 = sl.ahat2;
+  a.status = p->status;
+  if (!p->split) {
+    const TileOps& ops = tile_ops((int)p->n);
+    a.W = (int)W;
+    a.L = (int)p->n;
+    a.C = 1;
+    a.twf = p->tn.twf;
+    a.twi = p->tn.twi;
+    Launch fn = p->blocked ? ops.decode_split : ops.decode;
+    if (!fn) return FNT_RS_E_ARG;
+    fn(a, 1, st);
+    return cuda_ok(cudaGetLastError());
+  }
+  const int nbuf = dec_nbuf(p);
+  const size_t wc = split_chunk(p->n, nbuf);
+  const size_t nw = (size_t)p->n;
+  for (size_t c0 = 0; c0 < W; c0 += wc) {
+    const int w = (int)std::min(wc, W - c0);
+    uint32_t* A = static_cast<uint32_t*>(workspace);
+    uint32_t* B0 = A + nw * w;
+    uint32_t* B1 = B0 + nw * w;
+    uint32_t* B2 = B1 + nw * w;
+    KArgs c = a;
+    c.in = recv + c0;
+    c.out = out + c0;
+    c.W = w;
+    c.L = kLocalL;
+    c.C = p->C;
+    c.ld_work = (size_t)w;
+    c.powf = p->tn.powf;
+    c.powi = p->tn.powi;
+    c.twf = p->tl.twf;
+    c.twi = p->tl.twi;
+    auto cross = [&](bool inv, int lm, const void* in, size_t ld_in, int row_limit) {
+      KArgs x = c;
+      x.in = in;
+      x.ld_in = ld_in;
+      x.row_limit = row_limit;
+      x.out2 = A;
+      cross_launcher(p->C, inv, lm)(x, 1, st);
+    };
+    auto local = [&](bool inv, int mode, void* o2, void* o3, int out_limit, const void* in2) {
+      KArgs x = c;
+      x.in = A;
+      x.ld_in = (size_t)w;
+      x.out2 = o2;
+      x.out3 = o3;
+      x.in2 = in2;
+      x.out_limit = out_limit;
+      local_launcher(inv, mode)(x, p->C, st);
+    };
+    if (!p->blocked) {
+      cross(true, CL_RECV, recv + c0, ld_recv, (int)p->n);
+      local(true, LM_WORK, B0, nullptr, (int)p->k, nullptr);
+      cross(false, CL_U32, B0, (size_t)w, (int)p->k);
+      local(false, LM_WORK_AHAT, B0, nullptr, (int)p->n, nullptr);
+      cross(true, CL_U32, B0, (size_t)w, (int)p->n);
+      local(true, LM_OUT16, nullptr, nullptr, (int)p->k, nullptr);
+    } else {
+      const int h = (int)p->n / 2;
+      cross(true, CL_RECV, recv + c0, ld_recv, (int)p->n);
+      local(true, LM_SPLIT, B0, B1, (int)p->k, nullptr);
+      cross(false, CL_U32, B0, (size_t)w, h);
+      local(false, LM_X_PARTIAL, B0, B2, (int)p->n, nullptr);
+      cross(false, CL_U32, B1, (size_t)w, (int)p->k - h);
+      local(false, LM_ACCUM, nullptr, B2, (int)p->n, nullptr);
+      cross(true, CL_U32, B2, (size_t)w, (int)p->n);
+      local(true, LM_WORK, B1, nullptr, (int)p->n, nullptr);
+      cross(true, CL_U32, B0, (size_t)w, (int)p->n);
+      local(true, LM_OUT16_ADD, nullptr, nullptr, (int)p->k, B1);
+    }
+  }
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace fntrs
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* fnt_rs_strerror(int code) {
+  switch (code) {
+    case FNT_RS_OK: return "ok";
+    case FNT_RS_E_ARG: return "invalid argument";
+    case FNT_RS_E_UNSUPPORTED_P: return "unsupported field: p must be 65537";
+    case FNT_RS_E_ROOT: return "root does not have order exactly n";
+    case FNT_RS_E_POSITIONS: return "positions: fewer than k, duplicate, or >= n";
+    case FNT_RS_E_BUDGET: return "request exceeds the admission budget";
+    case FNT_RS_E_CUDA: return "CUDA runtime error";
+    case FNT_RS_E_RANGE: return "value out of range (decoded 65536 or received > 65536)";
+    case FNT_RS_E_TIMEOUT: return "a bounded device wait gave up";
+    case FNT_RS_E_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+uint64_t fnt_rs_launch_count(void) { return g_launches.load(); }
+
+int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, uint32_t root,
+                       void* stream) {
+  if (!out) return FNT_RS_E_ARG;
+  *out = nullptr;
+  if (n < 2 || n > 65536 || (n & (n - 1)) != 0 || k < 1 || k > n) return FNT_RS_E_ARG;
+  if (p_ != FNT_RS_P) return FNT_RS_E_UNSUPPORTED_P;
+  uint32_t u = 1;
+  if (root != 0) {
+    if (root >= FNT_RS_P || hpow(root, n) != 1 || hpow(root, n / 2) != FNT_RS_P - 1)
+      return FNT_RS_E_ROOT;
+    // root = default^u with u odd
+    const uint32_t r0 = default_root(n);
+    uint32_t acc = r0;
+    u = 0;
+    for (uint32_t e = 1; e < n; e += 2) {
+      if (acc == root) { u = e; break; }
+      acc = hmul(acc, hmul(r0, r0));
+    }
+    if (u == 0) return FNT_RS_E_ROOT;
+  }
+  init_ops();
+  fnt_rs_plan_s* p = new (std::nothrow) fnt_rs_plan_s();
+  if (!p) return FNT_RS_E_ARG;
+  cudaGetDevice(&p->dev);
+  p->n = n;
+  p->k = k;
+  p->root = root ? root : default_root(n);
+  p->u = u;
+  // inverse of the odd u modulo n (n is a power of two)
+  uint32_t ui = 1;
+  for (int it = 0; it < 5; ++it) ui = ui * (2u - u * ui);
+  p->uinv = ui & (n - 1);
+  p->ninv = hinv(n % FNT_RS_P);
+  p->split = n > (uint32_t)kTileMaxL;
+  p->C = p->split ? (int)(n / kLocalL) : 1;
+  p->blocked = k > n / 2;
+  int rc = get_tables((int)n, &p->tn);
+  if (!rc && p->split) rc = get_tables(kLocalL, &p->tl);
+  auto fail = [&](int code) {
+    fnt_rs_plan_destroy(p);
+    return code;
+  };
+  if (rc) return fail(rc);
+  if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess) return fail(FNT_RS_E_CUDA);
+  if (cudaMemsetAsync(p->status, 0, sizeof(int), S(stream)) != cudaSuccess)
+    return fail(FNT_RS_E_CUDA);
+  p->pscratch_words = pattern_scratch_words(n, k);
+  if (cudaMalloc(&p->pscratch, p->pscratch_words * 4) != cudaSuccess) return fail(FNT_RS_E_CUDA);
+  for (auto& sl : p->slots) {
+    if (cudaMalloc(&sl.pat, (size_t)n * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&sl.ahat, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&sl.ahat2, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&sl.pos_d, (size_t)n * 4) != cudaSuccess ||
+        cudaMallocHost(&sl.pos_h, (size_t)n * 4) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.staged, cudaEventDisableTiming) != cudaSuccess)
+      return fail(FNT_RS_E_CUDA);
+  }
+  if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return fail(FNT_RS_E_CUDA);
+  *out = p;
+  return FNT_RS_OK;
+}
+
+void fnt_rs_plan_destroy(fnt_rs_plan p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  cudaFree(p->status);
+  cudaFree(p->pscratch);
+  for (auto& sl : p->slots) {
+    cudaFree(sl.pat);
+    cudaFree(sl.ahat);
+    cudaFree(sl.ahat2);
+    cudaFree(sl.pos_d);
+    if (sl.pos_h) cudaFreeHost(sl.pos_h);
+    if (sl.staged) cudaEventDestroy(sl.staged);
+  }
+  delete p;
+}
+
+size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
+  if (!p) return 0;
+  switch (op) {
+    case FNT_RS_OP_ENCODE: return ws_bytes(p, W, enc_nbuf(p));
+    case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf(p));
+    case FNT_RS_OP_FNT: return ws_bytes(p, W, fnt_nbuf(p));
+    case FNT_RS_OP_ENCODE_HOST: {
+      const size_t stage = ((size_t)p->k * W * 2 + 255) / 256 * 256 + (size_t)p->n * W * 4;
+      return stage + ws_bytes(p, W, enc_nbuf(p));
+    }
+    case FNT_RS_OP_DECODE_HOST: {
+      const size_t stage = ((size_t)p->k * W * 4 + 255) / 256 * 256 + ((size_t)p->k * W * 2 + 255) / 256 * 256;
+      return stage + ws_bytes(p, W, dec_nbuf(p));
+    }
+    default: return 0;
+  }
+}
+
+static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+int fnt_rs_encode(fnt_rs_plan p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
+                  size_t W, void* workspace, void* stream) {
+  if (!p || W == 0) return W == 0 && p ? FNT_RS_OK : FNT_RS_E_ARG;
+  if (!src || !enc || ld_src < W || ld_enc < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if (!aligned(src, 2) || !aligned(enc, 4)) return FNT_RS_E_ARG;
+  if (ws_bytes(p, W, enc_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  return do_encode(p, src, ld_src, enc, ld_enc, W, workspace, S(stream));
+}
+
+int fnt_rs_decode_prepare(fnt_rs_plan p, const uint32_t* positions, uint32_t npos, void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  return prepare(p, positions, npos, S(stream));
+}
+
+int fnt_rs_decode(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv, const uint32_t* positions,
+                  uint32_t npos, uint16_t* out, size_t ld_out, size_t W, void* workspace,
+                  void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  if (!recv || !out || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if (!aligned(recv, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
+  if (ws_bytes(p, W, dec_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  int rc = prepare(p, positions, npos, S(stream));
+  if (rc) return rc;
+  if (W == 0) return FNT_RS_OK;
+  return do_decode(p, recv, ld_recv, out, ld_out, W, workspace, S(stream), 0);
+}
+
+int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
+                        const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
+                        size_t W, void* workspace, void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  if (!slots || !out || ld_slots < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if (!aligned(slots, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
+  if (ws_bytes(p, W, dec_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  if (p->u != 1) return FNT_RS_E_ROOT;  // slot rows follow the default root's positions
+  int rc = prepare(p, positions, npos, S(stream));
+  if (rc) return rc;
+  if (W == 0) return FNT_RS_OK;
+  return do_decode(p, slots, ld_slots, out, ld_out, W, workspace, S(stream), 1);
+}
+
+int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, size_t ld_out,
+               size_t W, int inverse, void* workspace, void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  if (W == 0) return FNT_RS_OK;
+  if (!in || !out || ld_in < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if (!aligned(in, 4) || !aligned(out, 4)) return FNT_RS_E_ARG;
+  if (ws_bytes(p, W, fnt_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  if (!p->split)
+    return run_fnt_default((int)p->n, in, ld_in, out, ld_out, (int)W, inverse != 0, p->uinv,
+                           nullptr, S(stream));
+  const size_t wc = split_chunk(p->n, 1);
+  for (size_t c0 = 0; c0 < W; c0 += wc) {
+    const int w = (int)std::min(wc, W - c0);
+    int rc = run_fnt_default((int)p->n, in + c0, ld_in, out + c0, ld_out, w, inverse != 0,
+                             p->uinv, static_cast<uint32_t*>(workspace), S(stream));
+    if (rc) return rc;
+  }
+  return FNT_RS_OK;
+}
+
+int fnt_rs_encode_host(fnt_rs_plan p, const uint16_t* h_src, uint32_t* h_enc, size_t W,
+                       void* workspace, void* stream) {
+  if (!p || !h_src || !h_enc || !workspace) return FNT_RS_E_ARG;
+  if (W == 0) return FNT_RS_OK;
+  cudaStream_t st = S(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  uint16_t* d_src = reinterpret_cast<uint16_t*>(ws);
+  uint32_t* d_enc = reinterpret_cast<uint32_t*>(ws + ((size_t)p->k * W * 2 + 255) / 256 * 256);
+  void* rest = reinterpret_cast<uint8_t*>(d_enc) + (size_t)p->n * W * 4;
+  int rc = cuda_ok(cudaMemcpyAsync(d_src, h_src, (size_t)p->k * W * 2, cudaMemcpyHostToDevice, st));
+  if (rc) return rc;
+  if ((rc = fnt_rs_encode(p, d_src, W, d_enc, W, W, rest, stream))) return rc;
+  if ((rc = cuda_ok(cudaMemcpyAsync(h_enc, d_enc, (size_t)p->n * W * 4, cudaMemcpyDeviceToHost, st))))
+    return rc;
+  return cuda_ok(cudaStreamSynchronize(st));
+}
+
+int fnt_rs_decode_host(fnt_rs_plan p, const uint32_t* h_recv, const uint32_t* positions,
+                       uint32_t npos, uint16_t* h_out, size_t W, void* workspace, void* stream) {
+  if (!p || !h_recv || !h_out || !workspace) return FNT_RS_E_ARG;
+  if (W == 0) return FNT_RS_OK;
+  cudaStream_t st = S(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  uint32_t* d_recv = reinterpret_cast<uint32_t*>(ws);
+  uint16_t* d_out = reinterpret_cast<uint16_t*>(ws + ((size_t)p->k * W * 4 + 255) / 256 * 256);
+  void* rest = reinterpret_cast<uint8_t*>(d_out) + ((size_t)p->k * W * 2 + 255) / 256 * 256;
+  int rc = cuda_ok(cudaMemcpyAsync(d_recv, h_recv, (size_t)p->k * W * 4, cudaMemcpyHostToDevice, st));
+  if (rc) return rc;
+  if ((rc = fnt_rs_decode(p, d_recv, W, positions, npos, d_out, W, W, rest, stream))) return rc;
+  if ((rc = cuda_ok(cudaMemcpyAsync(h_out, d_out, (size_t)p->k * W * 2, cudaMemcpyDeviceToHost, st))))
+    return rc;
+  return cuda_ok(cudaStreamSynchronize(st));
+}
+
+int fnt_rs_status(fnt_rs_plan p, void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  int h = 0;
+  cudaStream_t st = S(stream);
+  if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return FNT_RS_E_CUDA;
+  if (cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) return FNT_RS_E_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FNT_RS_E_CUDA;
+  if (h & ST_TIMEOUT) return FNT_RS_E_TIMEOUT;
+  if (h & ST_RANGE) return FNT_RS_E_RANGE;
+  return FNT_RS_OK;
+}
+
+int fnt_rs_plan_info(fnt_rs_plan p, int* info, int cap) {
+  if (!p || !info) return 0;
+  int vals[8] = {(int)p->n, (int)p->k, p->split ? kLocalL : (int)p->n, p->C,
+                 tile_ops(p->split ? kLocalL : (int)p->n).wt1,
+                 tile_ops(p->split ? kLocalL : (int)p->n).wt2, p->blocked ? 1 : 0, 0};
+  int cnt = 0;
+  for (auto& sl : p->slots) cnt += sl.valid ? 1 : 0;
+  vals[7] = cnt;
+  const int m = std::min(cap, 8);
+  for (int i = 0; i < m; ++i) info[i] = vals[i];
+  return m;
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// In-shared-memory batched FNT engine.
+//
+// A CTA transforms WT codewords of length L at once.  The length-L transform
+// (the FNT of Sec. II.A/II.B: A_j = sum_i a_i r^(ij)) is factored as
+// L = R1 * R2 * R3 (each radix <= 32, so every in-pass root is a power of two
+// and its products are rotations, see field.cuh).  One pass = every thread
+// loads the R values of a group into registers, runs a radix-R DFT there,
+// applies the inter-pass twiddles and writes back in place.  Decimation in
+// frequency (DIF) reads natural order and leaves the spectrum in
+// digit-reversed "slot" order; the transposed decimation-in-time (DIT) pass
+// sequence reads slot order and produces natural order.  The data between
+// passes live in shared memory as [slot][codeword] u32 with an XOR swizzle of
+// the slot index that keeps every pass free of bank conflicts.
+//
+// Slot layout after DIF pass p:  slot = j1*S1 + j2*S2 + j3   (S3 = 1)
+// holds spectrum index          j    = j1 + R1*j2 + R1*R2*j3.
+#pragma once
+#include "field.cuh"
+
+namespace fntrs {
+
+template <int L_, int R1_, int R2_ = 1, int R3_ = 1>
+struct Sched {
+  static constexpr int L = L_, R1 = R1_, R2 = R2_, R3 = R3_;
+  static_assert(R1 * R2 * R3 == L, "radices must multiply to L");
+  static constexpr int NP = (R3 > 1) ? 3 : ((R2 > 1) ? 2 : 1);
+  static constexpr int S1 = L / R1;
+  static constexpr int S2 = (NP == 3) ? S1 / R2 : 1;
+  static constexpr int RL = (NP == 3) ? R3 : ((NP == 2) ? R2 : R1);  // radix of last pass
+  // twiddle tables (entries): pass 1 -> L entries, pass 2 (3-pass only) -> S1 entries
+  static constexpr int TW2_OFF = L;
+  static constexpr int TW_ENTRIES = (NP == 1) ? 0 : (L + ((NP == 3) ? S1 : 0));
+
+  // spectrum index held by a slot in digit-reversed layout
+  static __device__ __forceinline__ int natural(int slot) {
+    if constexpr (NP == 1) {
+      return slot;
+    } else if constexpr (NP == 2) {
+      return slot / S1 + R1 * (slot % S1);
+    } else {
+      const int j1 = slot / S1, rem = slot % S1;
+      return j1 + R1 * (rem / S2) + R1 * R2 * (rem % S2);
+    }
+  }
+};
+
+// Shared-memory address of (slot, codeword c): swizzle the low bits of the
+// slot by the last-pass block index so that the 32/WT slot groups a warp
+// touches fall in different banks in every pass.
+template <class S, int WT>
+__device__ __forceinline__ int sm_addr(int slot, int c) {
+  constexpr int G = (WT >= 32) ? 1 : (32 / WT);
+  constexpr int SW = ((G < S::RL) ? G : S::RL) - 1;
+  constexpr int LB = ilog2(S::RL);
+  const int phys = slot ^ ((slot >> LB) & SW);
+  return phys * WT + c;
+}
+
+// multiply register q by table entry q (table entry 0 is always 1: skipped)
+template <int R>
+__device__ __forceinline__ void twiddle_regs(uint32_t* x, const uint32_t* __restrict__ tw) {
+  if constexpr (R >= 4) {
+#pragma unroll
+    for (int q = 0; q < R; q += 4) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(tw + q));
+      if (q != 0) x[q] = m_mul(x[q], w.x);
+      x[q + 1] = m_mul(x[q + 1], w.y);
+      x[q + 2] = m_mul(x[q + 2], w.z);
+      x[q + 3] = m_mul(x[q + 3], w.w);
+    }
+  } else {
+#pragma unroll
+    for (int q = 1; q < R; ++q) x[q] = m_mul(x[q], __ldg(tw + q));
+  }
+}
+
+// x_nat[j] = x[bitrev(j)]  (DIF output order -> natural, or the reverse)
+template <int R>
+__device__ __forceinline__ void bitrev_regs(uint32_t* x) {
+  constexpr int B = ilog2(R);
+  uint32_t y[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) y[j] = x[bitrev(j, B)];
+#pragma unroll
+  for (int j = 0; j < R; ++j) x[j] = y[j];
+}
+
+// ---------------------------------------------------------------------------
+// Pass building blocks.  Task loops run over (group g, codeword c), c fastest.
+// ---------------------------------------------------------------------------
+
+// DIF pass 1: natural-order input from a loader -> slots (or, for 1-pass
+// schedules, straight to the storer).
+//   load(i, c) -> value of input element i (0 <= i < L) of codeword c
+//   store(j, c, v) for 1-pass schedules: spectrum index j
+template <class S, int WT, int NT, bool INV, class Load, class Store>
+__device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restrict__ tw, Load& load,
+                                          Store& store) {
+  constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, i2 = t / WT;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = load(q * SP + i2, c);
+    dft_reg<R, INV>(x);
+    if constexpr (S::NP == 1) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) store(bitrev(q, B), c, x[q]);
+    } else {
+      twiddle_regs<R>(x, tw + i2 * R);
+#pragma unroll
+      for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
+    }
+  }
+}
+
+// DIF pass 2 of a 3-pass schedule, slots -> slots.
+template <class S, int WT, int NT, bool INV>
+__device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict__ tw2) {
+  constexpr int R = S::R2, SP = S::S2, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, g = t / WT;
+    const int b = g / SP, i2 = g % SP;
+    const int base = b * S::S1 + i2;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(base + q * SP, c)];
+    dft_reg<R, INV>(x);
+    twiddle_regs<R>(x, tw2 + i2 * R);
+#pragma unroll
+    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)] = x[q];
+  }
+}
+
+// Last DIF pass: slots -> storer, store(j, c, v) with j the spectrum index.
+template <class S, int WT, int NT, bool INV, class Store>
+__device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
+  static_assert(S::NP >= 2, "");
+  constexpr int R = S::RL, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, b = t / WT;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+    dft_reg<R, INV>(x);
+    const int base = S::natural(b * R);
+#pragma unroll
+    for (int q = 0; q < R; ++q) store(base + (S::L / R) * bitrev(q, B), c, x[q]);
+  }
+}
+
+// Last DIF pass writing back into the slots (for a following DIT sequence).
+template <class S, int WT, int NT, bool INV>
+__device__ __forceinline__ void dif_last_inplace(uint32_t* sm) {
+  static_assert(S::NP >= 2, "");
+  constexpr int R = S::RL;
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, b = t / WT;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+    dft_reg<R, INV>(x);
+    // register q holds spectrum digit bitrev(q): slot b*R + bitrev(q)
+    bitrev_regs<R>(x);
+#pragma unroll
+    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + q, c)] = x[q];
+  }
+}
+
+// DIT pass 2 of a 3-pass schedule (transposed DIF pass 2), slots -> slots.
+template <class S, int WT, int NT, bool INV>
+__device__ __forceinline__ void dit_mid(uint32_t* sm, const uint32_t* __restrict__ tw2) {
+  constexpr int R = S::R2, SP = S::S2, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, g = t / WT;
+    const int b = g / SP, i2 = g % SP;
+    const int base = b * S::S1 + i2;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)];
+    twiddle_regs<R>(x, tw2 + i2 * R);
+    bitrev_regs<R>(x);
+    dft_reg<R, INV>(x);
+#pragma unroll
+    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)] = x[q];
+  }
+}
+
+// DIT pass 1 (transposed DIF pass 1): slots -> natural order, handed to
+// store(i, c, v) with i the natural index.
+template <class S, int WT, int NT, bool INV, class Store>
+__device__ __forceinline__ void dit_first(uint32_t* sm, const uint32_t* __restrict__ tw,
+                                          Store& store) {
+  static_assert(S::NP >= 2, "");
+  constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, i2 = t / WT;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+    twiddle_regs<R>(x, tw + i2 * R);
+    bitrev_regs<R>(x);
+    dft_reg<R, INV>(x);
+#pragma unroll
+    for (int q = 0; q < R; ++q) store(bitrev(q, B) * SP + i2, c, x[q]);
+  }
+}
+
+// DIT last-group pass (the transpose of the last DIF pass) reading slots,
+// optionally multiplied by a second buffer slot-wise first, writing slots.
+template <class S, int WT, int NT, bool INV, bool MUL2>
+__device__ __forceinline__ void dit_last_inplace(uint32_t* sm, const uint32_t* sm2) {
+  static_assert(S::NP >= 2, "");
+  constexpr int R = S::RL, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, b = t / WT;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int a = sm_addr<S, WT>(b * R + q, c);
+      x[q] = MUL2 ? m_mul(sm[a], m_to_p(sm2[a])) : sm[a];
+    }
+    dft_reg<R, INV>(x);
+#pragma unroll
+    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
+  }
+}
+
+}  // namespace fntrs

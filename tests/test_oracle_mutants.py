@@ -39,7 +39,7 @@ MUTANTS = {
 def _build_mutant(tmp_path, name):
     old, new = MUTANTS[name]
     text = open(SRC).read()
-    assert text.count(old) == 1, name
+    assert text.count(old) >= 1, name
     path = tmp_path / f"{name}.c"
     path.write_text(text.replace(old, new))
     so = tmp_path / f"{name}.so"

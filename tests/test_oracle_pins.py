@@ -236,3 +236,15 @@ def test_bad_positions_rejected(oracle_lib):
         oracle_lib.decode(v, np.array([0, 1, 2, 16], dtype=np.uint32), n, k)  # out of range
     with pytest.raises(ValueError):
         oracle_lib.decode(v[:3], np.array([0, 1, 2], dtype=np.uint32), n, k)  # fewer than k
+
+
+def test_encode_rows_matches_definition(oracle_lib):
+    n, k = 64, 20
+    rng = np.random.default_rng(5)
+    s = rng.integers(0, 65536, size=(k, 3), dtype=np.uint16)
+    rows = np.array([0, 5, 63, 17], dtype=np.uint32)
+    got = oracle_lib.encode_rows(s, n, rows)
+    r = small.root(n)
+    for c in range(3):
+        full = small.dft_definition([int(v) for v in s[:, c]] + [0] * (n - k), r)
+        assert list(got[:, c]) == [full[j] for j in rows]
