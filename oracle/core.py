@@ -57,6 +57,8 @@ def _load():
             lib.orc_dft.restype = i32
             lib.orc_encode.argtypes = [u32, u32, u32, vp, sz, vp, sz, sz, i32]
             lib.orc_encode.restype = i32
+            lib.orc_encode_rows.argtypes = [u32, u32, u32, vp, sz, vp, u32, vp, sz, sz, i32]
+            lib.orc_encode_rows.restype = i32
             lib.orc_pattern.argtypes = [u32, u32, u32, vp, u32, vp, vp, vp]
             lib.orc_pattern.restype = i32
             lib.orc_decode.argtypes = [u32, u32, u32, vp, sz, vp, u32, vp, sz, sz,
@@ -89,6 +91,19 @@ def encode(src: np.ndarray, n: int, root_: int = 0, threads: int = 0) -> np.ndar
     rc = _load().orc_encode(n, k, root_, _ptr(src), W, _ptr(out), W, W, threads or max_threads())
     if rc:
         raise ValueError(f"orc_encode failed: {rc}")
+    return out
+
+
+def encode_rows(src: np.ndarray, n: int, rows, root_: int = 0, threads: int = 0) -> np.ndarray:
+    """e_j = s(r^j) at the given rows only: [len(rows)][W] uint32."""
+    src = np.ascontiguousarray(src, dtype=np.uint16)
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    k, W = src.shape
+    out = np.empty((len(rows), W), dtype=np.uint32)
+    rc = _load().orc_encode_rows(n, k, root_, _ptr(src), W, _ptr(rows), len(rows), _ptr(out), W,
+                                 W, threads or max_threads())
+    if rc:
+        raise ValueError(f"orc_encode_rows failed: {rc}")
     return out
 
 

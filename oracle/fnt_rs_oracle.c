@@ -16,6 +16,7 @@
  *   orc_dft          DFT / inverse DFT by definition               (Sec. II.A, DFT displays)
  *   orc_encode       e_i = s(r^i), Horner evaluation per codeword  (Sec. II.B, e_i = s(r^i);
  *                    FNT as evaluation on 1, r, ..., r^{n-1}: Sec. II.A)
+ *   orc_encode_rows  the same at selected rows only
  *   orc_pattern      A(x) = prod_j (x - x_j), A'(x), A'(x_i), and
  *                    1 / A'(x_i) = 1 / A_i(x_i)                    (Sec. II.B, Lagrange
  *                                                                   rewrite and derivative identity)
@@ -125,6 +126,30 @@ int orc_encode(uint32_t n, uint32_t k, uint32_t root, const uint16_t* src, size_
       for (uint32_t i = k; i-- > 0;) acc = orc_add(orc_mul(acc, x), src[(size_t)i * ld_src + c]);
       enc[(size_t)j * ld_enc + c] = acc;
       x = orc_mul(x, r);
+    }
+  }
+  return ORC_OK;
+}
+
+/*
+ * The same definition, e_j = s(r^j), evaluated only at the rows listed in
+ * `rows` (Horner, O(k) per entry); out: [nrows][ld_out].
+ */
+int orc_encode_rows(uint32_t n, uint32_t k, uint32_t root, const uint16_t* src, size_t ld_src,
+                    const uint32_t* rows, uint32_t nrows, uint32_t* out, size_t ld_out, size_t W,
+                    int nthreads) {
+  if (!is_pow2_n(n) || k < 1 || k > n || !src || !out || !rows) return ORC_ARG;
+  uint32_t r = root ? root : orc_root(n);
+  (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (long long c = 0; c < (long long)W; ++c) {
+    for (uint32_t t = 0; t < nrows; ++t) {
+      uint32_t x = orc_pow(r, rows[t]);
+      uint32_t acc = 0;
+      for (uint32_t i = k; i-- > 0;) acc = orc_add(orc_mul(acc, x), src[(size_t)i * ld_src + c]);
+      out[(size_t)t * ld_out + c] = acc;
     }
   }
   return ORC_OK;
