@@ -52,10 +52,12 @@ __device__ __forceinline__ uint32_t m_mul(uint32_t x, uint32_t w) {
   return m_add(x * w, __umulhi(x, w));
 }
 
-// Reduce an element of Z/M to its representative in [0, p) = [0, 65536].
+// Reduce an element of Z/M to its representative in [0, p) = [0, 65536]:
+// t = lo - hi (2^16 = -1) lies in (-2^16, 2^16); as unsigned words the
+// smaller of t and t + p is the one in range.
 __device__ __forceinline__ uint32_t m_to_p(uint32_t x) {
-  int32_t t = (int32_t)(x & 0xFFFFu) - (int32_t)(x >> 16);
-  return (uint32_t)(t + ((t >> 31) & (int32_t)kP));
+  const uint32_t t = x - (x >> 16) * kP;
+  return min(t, t + kP);
 }
 
 // Exponentiation in F_p (canonical inputs < p); used for per-pattern inverses.

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+
 #include "kernels.cuh"
 #include "sched.h"
 
@@ -35,7 +37,7 @@ inline void ensure_smem(void (*kern)(KArgs), int bytes) {
 template <class S, int WT, int NT, bool INV, class LD, class ST>
 void launch_tile(const KArgs& a, int gy, cudaStream_t st) {
   auto kern = k_tile<S, WT, NT, INV, LD, ST>;
-  const int smem = S::NP >= 2 ? S::L * WT * 4 : 0;
+  const int smem = smem_words<S, WT>() * 4;
   struct Tag {};
   ensure_smem<Tag>(kern, smem);
   dim3 grid((a.W + WT - 1) / WT, gy);
@@ -46,7 +48,7 @@ void launch_tile(const KArgs& a, int gy, cudaStream_t st) {
 template <class S, int WT, int NT>
 void launch_decode(const KArgs& a, int, cudaStream_t st) {
   auto kern = k_decode<S, WT, NT>;
-  const int smem = S::NP >= 2 ? S::L * WT * 4 : 0;
+  const int smem = smem_words<S, WT>() * 4;
   struct Tag {};
   ensure_smem<Tag>(kern, smem);
   dim3 grid((a.W + WT - 1) / WT, 1);
@@ -57,7 +59,7 @@ void launch_decode(const KArgs& a, int, cudaStream_t st) {
 template <class S, int WT, int NT>
 void launch_decode_split(const KArgs& a, int, cudaStream_t st) {
   auto kern = k_decode_split<S, WT, NT>;
-  const int smem = 2 * S::L * WT * 4;
+  const int smem = 2 * smem_words<S, WT>() * 4;
   struct Tag {};
   ensure_smem<Tag>(kern, smem);
   dim3 grid((a.W + WT - 1) / WT, 1);
@@ -68,7 +70,7 @@ void launch_decode_split(const KArgs& a, int, cudaStream_t st) {
 template <class S, int WT, int NT>
 void launch_poly_level(const KArgs& a, int, cudaStream_t st) {
   auto kern = k_poly_level<S, WT, NT>;
-  const int smem = 2 * S::L * WT * 4;
+  const int smem = 2 * smem_words<S, WT>() * 4;
   struct Tag {};
   ensure_smem<Tag>(kern, smem);
   const int npairs = (a.nodes + 1) / 2;
@@ -96,5 +98,30 @@ TileOps make_tile_ops() {
 }
 
 void register_ops(const TileOps& ops);
+
+// Persistent TMA-staged encode (k_encode_tma): dynamic shared memory bytes.
+template <class S, int WT>
+constexpr int encode_tma_smem(int rows_staged) {
+  return ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128 + rows_staged * WT * 2 + 16;
+}
+
+template <class S, int WT, int NT, int C>
+int launch_encode_tma_t(const KArgs& a, const uint32_t* twc, int rows_staged, int box_rows,
+                        const CUtensorMap& map, int grid, cudaStream_t st) {
+  auto kern = k_encode_tma<S, WT, NT, C>;
+  const int smem = encode_tma_smem<S, WT>(rows_staged);
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!done[dev & 63]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             encode_tma_smem<S, WT>(S::L)) != cudaSuccess)
+      return -1;
+    done[dev & 63] = true;
+  }
+  kern<<<grid, NT, smem, st>>>(a, twc, rows_staged, box_rows, map);
+  count_launch();
+  return 0;
+}
 
 }  // namespace fntrs

@@ -3,6 +3,7 @@
 #pragma once
 #include "kargs.h"
 #include "tile.cuh"
+#include "tma.cuh"
 
 namespace fntrs {
 
@@ -21,13 +22,12 @@ struct LoadSrcFold {
   const uint32_t* powf;
   int col0, W, k, L, C, cc, eC, nmask;
   static __device__ __forceinline__ LoadSrcFold make(const KArgs& a) {
-    int eC = 0;
-    for (int c = a.C; c > 1; c >>= 1) eC += 1;  // log2(C)
+    int lc = 0;
+    for (int c = a.C; c > 1; c >>= 1) lc += 1;  // log2(C)
     // e_C for C = 2,4,8,16: 16, 24, 12, 6  (2^e_C = 3^(65536/C) mod p)
-    const int tab[5] = {0, 16, 24, 12, 6};
+    const int eC = lc == 0 ? 0 : (lc == 1 ? 16 : (lc == 2 ? 24 : (lc == 3 ? 12 : 6)));
     return LoadSrcFold{static_cast<const uint16_t*>(a.in), a.ld_in, a.powf,
-                       (int)blockIdx.x * WT, a.W, a.k, a.L, a.C, (int)blockIdx.y,
-                       tab[eC], a.n - 1};
+                       (int)blockIdx.x * WT, a.W, a.k, a.L, a.C, (int)blockIdx.y, eC, a.n - 1};
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) const {
     const int col = col0 + c;
@@ -66,28 +66,34 @@ struct LoadRows32 {
 
 // Decode step 4 + the scatter of step 5 (Sec. II.B): the length-n vector
 // u[z] = v_i * c_i at z = z_i (the first k received positions), 0 elsewhere,
-// with c_i = -r^(-z_i) / A'(r^(z_i)) from the pattern table.
+// with c_i = -r^(-z_i) / A'(r^(z_i)) from the pattern table (weight 0 marks
+// an unused position).  Received values above 65536 are flagged once per
+// thread at the end of the kernel (see flush()).
 template <int WT>
 struct LoadRecv {
   const uint32_t* recv;
   size_t ld;
   const uint2* pat;
   int* status;
-  size_t z0;
   int col0, W, slots;
+  uint32_t bad;
   static __device__ __forceinline__ LoadRecv make(const KArgs& a) {
-    return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status, 0,
-                    (int)blockIdx.x * WT, a.W, a.slots};
+    return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status,
+                    (int)blockIdx.x * WT, a.W, a.slots, 0u};
   }
-  __device__ __forceinline__ uint32_t operator()(int i, int c) const {
+  __device__ __forceinline__ uint32_t operator()(int i, int c) {
     const int col = col0 + c;
-    if (col >= W) return 0u;
-    const uint2 e = __ldg(pat + z0 + i);
-    if ((int)e.x < 0) return 0u;
-    const size_t row = slots ? (size_t)(z0 + i) : (size_t)e.x;
-    const uint32_t v = recv[row * ld + col];
-    if (v > 65536u) atomicOr(status, ST_RANGE);
+    const uint2 e = __ldg(pat + i);
+    uint32_t v = 0u;
+    if (e.y != 0u && col < W) {
+      const size_t row = slots ? (size_t)i : (size_t)e.x;
+      v = recv[row * ld + col];
+    }
+    bad |= v > 65536u ? 1u : 0u;
     return m_mul(v, e.y);
+  }
+  __device__ __forceinline__ void flush() const {
+    if (bad) atomicOr(status, ST_RANGE);
   }
 };
 
@@ -116,12 +122,10 @@ struct StoreRows32 {
   }
 };
 
-__device__ __forceinline__ uint16_t to_symbol(uint32_t v, int* status) {
+// Reduce to [0, p); 65536 (no 16-bit symbol) becomes 0 and sets `bad`.
+__device__ __forceinline__ uint16_t to_symbol(uint32_t v, uint32_t& bad) {
   const uint32_t r = m_to_p(v);
-  if (r == 65536u) {
-    atomicOr(status, ST_RANGE);
-    return 0;
-  }
+  bad |= r >> 16;
   return (uint16_t)r;
 }
 
@@ -131,16 +135,18 @@ template <int WT, int MODE>
 struct StoreLocal {
   KArgs a;
   int col0, j1;
+  uint32_t bad;
   static __device__ __forceinline__ StoreLocal make(const KArgs& a) {
-    return StoreLocal{a, (int)blockIdx.x * WT, (int)blockIdx.y};
+    return StoreLocal{a, (int)blockIdx.x * WT, (int)blockIdx.y, 0u};
   }
-  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
     if (col >= a.W) return;
     const size_t row = (size_t)j1 + (size_t)a.C * j;
     if constexpr (MODE == LM_ENC || MODE == LM_FNT) {
       if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
-      const size_t orow = a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
+      const size_t orow =
+          a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
       static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
     } else if constexpr (MODE == LM_WORK) {
       if ((int)row < a.out_limit) static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
@@ -148,7 +154,7 @@ struct StoreLocal {
       static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(v, __ldg(a.ahat + row));
     } else if constexpr (MODE == LM_OUT16) {
       if ((int)row < a.out_limit)
-        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, a.status);
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
     } else if constexpr (MODE == LM_SPLIT) {
       if ((int)row < a.h)
         static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
@@ -165,15 +171,25 @@ struct StoreLocal {
       if ((int)row < a.out_limit) {
         if ((int)row >= a.h)
           v = m_add(v, static_cast<const uint32_t*>(a.in2)[(row - a.h) * a.ld_work + col]);
-        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, a.status);
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
       }
     }
   }
+  __device__ __forceinline__ void flush() const {
+    if (bad) atomicOr(a.status, ST_RANGE);
+  }
 };
+
+template <class T>
+__device__ __forceinline__ auto flush_if_any(const T& t, int) -> decltype(t.flush(), void()) {
+  t.flush();
+}
+template <class T>
+__device__ __forceinline__ void flush_if_any(const T&, long) {}
 
 // ---------------------------------------------------------------------------
 // Generic tile transform: DIF passes from a loader to a storer.
-// grid = (ceil(W / WT), classes or blocks), dynamic smem = L * WT * 4 bytes.
+// grid = (ceil(W / WT), classes or blocks), dynamic smem = Lay WORDS * 4 bytes.
 // ---------------------------------------------------------------------------
 template <class S, int WT, int NT, bool INV, class LD, class ST>
 __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
@@ -191,6 +207,127 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
     }
     dif_last<S, WT, NT, INV>(sm, store);
   }
+  flush_if_any(store, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent encode with TMA-staged source (n = C * L, C in {1, 2}, k <= L).
+// Each CTA walks column tiles of WT codewords; the [k][WT] source tile is
+// brought into shared memory by cp.async.bulk.tensor while the previous tile
+// is still being transformed.  For C = 2 the tile feeds both output classes:
+// class 1 takes x[i] = s_i r_n^i; with i = q*S1 + i2 the factor r_n^(q*S1) is
+// a power of two (r_n^S1 has order 2*R1 <= 32) and r_n^i2 rides on the pass-1
+// twiddle table twc (all R1 entries).
+// smem: work (Lay WORDS u32) | stage (rows_staged * WT u16) | mbarrier.
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT, int C>
+__global__ void __launch_bounds__(NT, 1)
+    k_encode_tma(KArgs a, const uint32_t* __restrict__ twc, int rows_staged, int box_rows,
+                 const __grid_constant__ CUtensorMap tsrc) {
+  static_assert(S::NP == 3 || S::NP == 2, "");
+  static_assert(C == 1 || (C == 2 && 2 * S::R1 <= 32), "");
+  using Y = Lay<S, WT>;
+  constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+  constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
+  extern __shared__ __align__(128) uint4 smem_raw[];
+  uint32_t* work = reinterpret_cast<uint32_t*>(smem_raw);
+  uint16_t* stage = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(stage) +
+                                              (size_t)rows_staged * WT * 2);
+  const int ntiles = (a.W + WT - 1) / WT;
+  const int nbox = rows_staged / box_rows;
+  const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 2;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+    mbar_expect_tx(bar, tx_bytes);
+    for (int bx = 0; bx < nbox; ++bx)
+      tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, (int)blockIdx.x * WT, bx * box_rows,
+                  bar);
+  }
+  uint32_t parity = 0;
+  uint32_t* out = static_cast<uint32_t*>(a.out);
+  const size_t ld = a.ld_out;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool ok = mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        mbar_wait(bar, parity);  // let the copy in flight land before exiting
+      }
+      return;
+    }
+    parity ^= 1u;
+    const int col0 = tile * WT;
+#pragma unroll 1
+    for (int cc = 0; cc < C; ++cc) {
+      // pass 1 from the staged source
+      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+        const int c = t % WT, i2 = t / WT;
+        uint32_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int row = q * SP + i2;
+          x[q] = row < rows_staged ? (uint32_t)stage[row * WT + c] : 0u;
+        }
+        if (C == 2 && cc == 1) {
+          constexpr int e = Pow2Root<(2 * R > 32 ? 32 : 2 * R)>::e;
+#pragma unroll
+          for (int q = 1; q < R; ++q) x[q] = m_rot_rt(x[q], (uint32_t)(e * q));
+        }
+        dft_reg<R, false>(x);
+        if (C == 2 && cc == 1) {
+          const uint4* tw4 = reinterpret_cast<const uint4*>(twc + i2 * R);
+#pragma unroll
+          for (int q = 0; q < R; q += 4) {
+            const uint4 w = __ldg(tw4 + q / 4);
+            x[q] = m_mul(x[q], w.x);
+            x[q + 1] = m_mul(x[q + 1], w.y);
+            x[q + 2] = m_mul(x[q + 2], w.z);
+            x[q + 3] = m_mul(x[q + 3], w.w);
+          }
+        } else {
+          twiddle_regs<R>(x, a.twf + i2 * R);
+        }
+        uint32_t* base = work + Y::addr(i2, c);
+#pragma unroll
+        for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
+      }
+      __syncthreads();
+      if (cc == C - 1 && threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+        // the stage is free: prefetch the next tile
+        fence_proxy_async();
+        mbar_expect_tx(bar, tx_bytes);
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, (tile + (int)gridDim.x) * WT,
+                      bx * box_rows, bar);
+      }
+      if constexpr (S::NP == 3) {
+        dif_mid<S, WT, NT, false>(work, a.twf + S::TW2_OFF);
+        __syncthreads();
+      }
+      // last pass -> encoded rows cc + C*j
+      {
+        constexpr int RL = S::RL, BL = ilog2(RL);
+        for (int t = threadIdx.x; t < (S::L / RL) * WT; t += NT) {
+          const int c = t % WT, b = t / WT;
+          const uint32_t* base = work + b * Y::LAST_B + c;
+          uint32_t x[RL];
+#pragma unroll
+          for (int q = 0; q < RL; ++q) x[q] = base[q * WT];
+          dft_reg<RL, false>(x);
+          const int col = col0 + c;
+          if (col < a.W) {
+            uint32_t* o = out + (size_t)(cc + C * S::natural(b * RL)) * ld + col;
+            const size_t step = (size_t)C * (S::L / RL) * ld;
+#pragma unroll
+            for (int q = 0; q < RL; ++q) o[bitrev(q, BL) * step] = m_to_p(x[q]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -205,30 +342,33 @@ __global__ void __launch_bounds__(256) k_cross(KArgs a) {
   const long long i2l = t / a.W;
   if (i2l >= a.L) return;
   const int i2 = (int)i2l;
+  uint32_t bad = 0u;
   uint32_t x[C];
 #pragma unroll
   for (int q = 0; q < C; ++q) {
     const int row = q * a.L + i2;
     if constexpr (LOADM == CL_SRC16) {
-      x[q] = row < a.row_limit ? (uint32_t)static_cast<const uint16_t*>(a.in)[(size_t)row * a.ld_in + col]
-                               : 0u;
+      x[q] = row < a.row_limit
+                 ? (uint32_t) static_cast<const uint16_t*>(a.in)[(size_t)row * a.ld_in + col]
+                 : 0u;
     } else if constexpr (LOADM == CL_U32) {
-      const uint32_t r = a.in_row_mul == 1u ? (uint32_t)row
-                                            : ((a.in_row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
+      const uint32_t r = a.in_row_mul == 1u
+                             ? (uint32_t)row
+                             : ((a.in_row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
       x[q] = row < a.row_limit ? static_cast<const uint32_t*>(a.in)[(size_t)r * a.ld_in + col]
                                : 0u;
     } else {
       const uint2 e = __ldg(a.pat + row);
       uint32_t v = 0u;
-      if ((int)e.x >= 0) {
+      if (e.y != 0u) {
         const size_t rr = a.slots ? (size_t)row : (size_t)e.x;
         v = static_cast<const uint32_t*>(a.in)[rr * a.ld_in + col];
-        if (v > 65536u) atomicOr(a.status, ST_RANGE);
-        v = m_mul(v, e.y);
       }
-      x[q] = v;
+      bad |= v > 65536u ? 1u : 0u;
+      x[q] = m_mul(v, e.y);
     }
   }
+  if (bad) atomicOr(a.status, ST_RANGE);
   dft_reg<C, INV>(x);
   const uint32_t* pw = INV ? a.powi : a.powf;
   constexpr int B = ilog2(C);
@@ -256,21 +396,30 @@ struct StoreOut16 {
   size_t ld;
   int* status;
   int col0, W, k;
+  uint32_t bad;
   static __device__ __forceinline__ StoreOut16 make(const KArgs& a) {
     return StoreOut16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, (int)blockIdx.x * WT,
-                      a.W, a.k};
+                      a.W, a.k, 0u};
   }
-  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
     if (col >= W || j >= k) return;
-    out[(size_t)j * ld + col] = to_symbol(v, status);
+    out[(size_t)j * ld + col] = to_symbol(v, bad);
   }
+  __device__ __forceinline__ void flush() const {
+    if (bad) atomicOr(status, ST_RANGE);
+  }
+};
+
+struct NopStore {
+  __device__ __forceinline__ void operator()(int, int, uint32_t) const {}
 };
 
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  using Y = Lay<S, WT>;
   LoadRecv<WT> load = LoadRecv<WT>::make(a);
   StoreOut16<WT> store = StoreOut16<WT>::make(a);
   const uint32_t* __restrict__ ahat = a.ahat;
@@ -296,13 +445,9 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
   } else {
     const uint32_t* tw1f = a.twf;
     const uint32_t* tw1i = a.twi;
+    NopStore nop;
     // D1 passes (root r^-1), natural -> slots
-    {
-      struct Nop {
-        __device__ void operator()(int, int, uint32_t) const {}
-      } nop;
-      dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
-    }
+    dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
     __syncthreads();
     if constexpr (S::NP == 3) {
       dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
@@ -313,18 +458,19 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
       constexpr int R = S::RL, B = ilog2(R);
       for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
         const int c = t % WT, b = t / WT;
+        uint32_t* base = sm + b * Y::LAST_B + c;
         uint32_t x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+        for (int q = 0; q < R; ++q) x[q] = base[q * WT];
         dft_reg<R, true>(x);
-        const int base = S::natural(b * R);
+        const int j0 = S::natural(b * R);
 #pragma unroll
         for (int q = 0; q < R; ++q)
-          if (base + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
+          if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
         bitrev_regs<R>(x);
         dft_reg<R, false>(x);
 #pragma unroll
-        for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
+        for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
       }
     }
     __syncthreads();
@@ -337,9 +483,10 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
       constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
       for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
         const int c = t % WT, i2 = t / WT;
+        uint32_t* base = sm + Y::addr(i2, c);
         uint32_t x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+        for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
         twiddle_regs<R>(x, tw1f + i2 * R);
         bitrev_regs<R>(x);
         dft_reg<R, false>(x);
@@ -349,7 +496,7 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
         dft_reg<R, true>(x);
         twiddle_regs<R>(x, tw1i + i2 * R);
 #pragma unroll
-        for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
+        for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
       }
     }
     __syncthreads();
@@ -359,6 +506,8 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
     }
     dif_last<S, WT, NT, true>(sm, store);
   }
+  load.flush();
+  store.flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -368,6 +517,7 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
 // Buffers X (S0 path) and Y (S1 path) in shared memory; ahat = n^-1 FNT(A0),
 // ahat2 = n^-1 FNT(A1).  Output P_j = X_j + (j >= h ? Y_(j-h) : 0).
 // ---------------------------------------------------------------------------
+
 // One codeword per thread, everything in registers (L <= 32).
 template <int L, int WT, int NT>
 __device__ __forceinline__ void decode_split_regs(const KArgs& a) {
@@ -409,23 +559,22 @@ __device__ __forceinline__ void decode_split_regs(const KArgs& a) {
       store(j, c, v);
     }
   }
+  load.flush();
+  store.flush();
 }
 
 template <class S, int WT, int NT>
 __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
+  using Y = Lay<S, WT>;
   extern __shared__ uint4 smem_raw[];
   uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* Y = X + S::L * WT;
+  uint32_t* Yb = X + Y::WORDS;
   LoadRecv<WT> load = LoadRecv<WT>::make(a);
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
-  const int k = a.k, h = S::L / 2;
-  {
-    struct Nop {
-      __device__ void operator()(int, int, uint32_t) const {}
-    } nop;
-    dif_first<S, WT, NT, true>(X, tw1i, load, nop);
-  }
+  const int k = a.k;
+  NopStore nop;
+  dif_first<S, WT, NT, true>(X, tw1i, load, nop);
   __syncthreads();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(X, tw1i + S::TW2_OFF);
@@ -436,15 +585,16 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
     constexpr int R = S::RL, B = ilog2(R), HR = R / 2;
     for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
       const int c = t % WT, b = t / WT;
+      const int off = b * Y::LAST_B + c;
       uint32_t x[R], y[R];
 #pragma unroll
-      for (int q = 0; q < R; ++q) x[q] = X[sm_addr<S, WT>(b * R + q, c)];
+      for (int q = 0; q < R; ++q) x[q] = X[off + q * WT];
       dft_reg<R, true>(x);
       bitrev_regs<R>(x);  // x[d] = digit d
-      const int base = S::natural(b * R);
+      const int j0 = S::natural(b * R);
 #pragma unroll
       for (int d = 0; d < HR; ++d) {
-        y[d] = (base + (S::L / R) * (d + HR) < k) ? x[d + HR] : 0u;
+        y[d] = (j0 + (S::L / R) * (d + HR) < k) ? x[d + HR] : 0u;
         y[d + HR] = 0u;
         x[d + HR] = 0u;
       }
@@ -452,15 +602,15 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
       dft_reg<R, false>(y);
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        X[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
-        Y[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = y[q];
+        X[off + bitrev(q, B) * WT] = x[q];
+        Yb[off + bitrev(q, B) * WT] = y[q];
       }
     }
   }
   __syncthreads();
   if constexpr (S::NP == 3) {
     dit_mid<S, WT, NT, false>(X, tw1f + S::TW2_OFF);
-    dit_mid<S, WT, NT, false>(Y, tw1f + S::TW2_OFF);
+    dit_mid<S, WT, NT, false>(Yb, tw1f + S::TW2_OFF);
     __syncthreads();
   }
   // last D2 pass on both, Xf = S0^ A0^, Yf = S1^ A0^ + S0^ A1^, first D3 pass on both
@@ -468,11 +618,12 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
     constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
     for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
       const int c = t % WT, i2 = t / WT;
+      const int off = Y::addr(i2, c);
       uint32_t x[R], y[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        x[q] = X[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
-        y[q] = Y[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+        x[q] = X[off + bitrev(q, B) * Y::P1_STRIDE];
+        y[q] = Yb[off + bitrev(q, B) * Y::P1_STRIDE];
       }
       twiddle_regs<R>(x, tw1f + i2 * R);
       twiddle_regs<R>(y, tw1f + i2 * R);
@@ -496,18 +647,19 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
       twiddle_regs<R>(y, tw1i + i2 * R);
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        X[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
-        Y[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = y[q];
+        X[off + bitrev(q, B) * Y::P1_STRIDE] = x[q];
+        Yb[off + bitrev(q, B) * Y::P1_STRIDE] = y[q];
       }
     }
   }
   __syncthreads();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(X, tw1i + S::TW2_OFF);
-    dif_mid<S, WT, NT, true>(Y, tw1i + S::TW2_OFF);
+    dif_mid<S, WT, NT, true>(Yb, tw1i + S::TW2_OFF);
     __syncthreads();
   }
   // last D3 pass on both; P_j = X_j + (j >= h ? Y_(j-h) : 0)
+  uint32_t bad = 0u;
   {
     constexpr int R = S::RL, HR = R / 2;
     uint16_t* out = static_cast<uint16_t*>(a.out);
@@ -515,29 +667,31 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
     for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
       const int c = t % WT, b = t / WT;
       const int col = col0 + c;
+      const int off = b * Y::LAST_B + c;
       uint32_t x[R], y[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        x[q] = X[sm_addr<S, WT>(b * R + q, c)];
-        y[q] = Y[sm_addr<S, WT>(b * R + q, c)];
+        x[q] = X[off + q * WT];
+        y[q] = Yb[off + q * WT];
       }
       dft_reg<R, true>(x);
       dft_reg<R, true>(y);
       bitrev_regs<R>(x);
       bitrev_regs<R>(y);
-      const int base = S::natural(b * R);
+      const int j0 = S::natural(b * R);
       if (col < a.W) {
 #pragma unroll
         for (int d = 0; d < R; ++d) {
-          const int j = base + (S::L / R) * d;
+          const int j = j0 + (S::L / R) * d;
           uint32_t v = x[d];
           if (d >= HR) v = m_add(v, y[d - HR]);
-          if (j < k) out[(size_t)j * a.ld_out + col] = to_symbol(v, a.status);
+          if (j < k) out[(size_t)j * a.ld_out + col] = to_symbol(v, bad);
         }
       }
     }
   }
-  (void)h;
+  load.flush();
+  if (bad) atomicOr(a.status, ST_RANGE);
 }
 
 template <class S, int WT, int NT>
@@ -560,9 +714,10 @@ __global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT) k_poly_level(KArgs a) {
   static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
   extern __shared__ uint4 smem_raw[];
   uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* Y = X + S::L * WT;
+  uint32_t* Yb = X + Y::WORDS;
   const uint32_t* lvl = static_cast<const uint32_t*>(a.in);
   const size_t ldl = a.ld_in;  // = nodes
   const int d = a.deg_child, nodes = a.nodes, k = a.k;
@@ -577,24 +732,22 @@ __global__ void __launch_bounds__(NT) k_poly_level(KArgs a) {
       return i <= d ? lvl[(size_t)i * ld + node] : 0u;
     }
   };
-  struct Nop {
-    __device__ void operator()(int, int, uint32_t) const {}
-  } nop;
+  NopStore nop;
   const uint32_t* twf = a.twf;
   const uint32_t* twi = a.twi;
   LoadChild la{lvl, ldl, d, nodes, p0, 0}, lb{lvl, ldl, d, nodes, p0, 1};
   dif_first<S, WT, NT, false>(X, twf, la, nop);
-  dif_first<S, WT, NT, false>(Y, twf, lb, nop);
+  dif_first<S, WT, NT, false>(Yb, twf, lb, nop);
   __syncthreads();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, false>(X, twf + S::TW2_OFF);
-    dif_mid<S, WT, NT, false>(Y, twf + S::TW2_OFF);
+    dif_mid<S, WT, NT, false>(Yb, twf + S::TW2_OFF);
     __syncthreads();
   }
   dif_last_inplace<S, WT, NT, false>(X);
-  dif_last_inplace<S, WT, NT, false>(Y);
+  dif_last_inplace<S, WT, NT, false>(Yb);
   __syncthreads();
-  dit_last_inplace<S, WT, NT, true, true>(X, Y);
+  dit_last_inplace<S, WT, NT, true, true>(X, Yb);
   __syncthreads();
   if constexpr (S::NP == 3) {
     dit_mid<S, WT, NT, true>(X, twi + S::TW2_OFF);

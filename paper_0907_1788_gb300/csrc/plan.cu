@@ -1,5 +1,7 @@
 // Host side of libfntrs: plans, twiddle tables, pattern cache, dispatch and
 // the C ABI declared in include/fnt_rs.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +48,31 @@ const TileOps& tile_ops(int L) {
   int b = 0;
   while ((1 << b) < L) ++b;
   return g_ops[b];
+}
+
+int launch_encode_tma_small(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
+int launch_encode_tma_mid(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
+int launch_encode_tma_big(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
+
+int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st) {
+  if (L <= 256) return launch_encode_tma_small(L, C, a, t, st);
+  if (L <= 2048) return launch_encode_tma_mid(L, C, a, t, st);
+  return launch_encode_tma_big(L, C, a, t, st);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
 }
 
 void launch_pat_init(uint2* pat, int n, cudaStream_t st);
@@ -195,6 +222,11 @@ struct fnt_rs_plan_s {
   bool blocked = false;  // k > n/2
   Tables tn;             // tables of length n (pow tables; schedule tables if n <= tile)
   Tables tl;             // tables of the local length (split only)
+  Tables tenc;           // schedule tables of the TMA encode's tile length
+  uint32_t* twc = nullptr;  // TMA encode, class 1 of n = 2L: pass-1 twiddles times r_n^i2
+  int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
+  bool no_tma = false;
+  int sms = 1;
   int* status = nullptr;
   uint32_t* pscratch = nullptr;
   size_t pscratch_words = 0;
@@ -406,8 +438,51 @@ static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, c
 // ---------------------------------------------------------------------------
 // encode / decode / fnt dispatch
 // ---------------------------------------------------------------------------
+// Persistent TMA-staged encode; returns 1 if it was not applicable.
+static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                      size_t ld_enc, size_t W, cudaStream_t st) {
+  if (p->no_tma || p->enc_L == 0 || p->u != 1) return 1;
+  if ((reinterpret_cast<uintptr_t>(src) % 16) != 0 || (ld_src * 2) % 16 != 0) return 1;
+  auto fn = tmap_encode_fn();
+  if (!fn) return 1;
+  const int L = p->enc_L, C = p->enc_C;
+  const int WT = tile_ops(L).wt1;
+  const int box_rows = std::min(256, L);
+  const int rows_staged = (int)((p->k + box_rows - 1) / box_rows) * box_rows;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)p->k};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld_src * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)WT, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(src), dims, strides, box,
+         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 1;
+  const int ntiles = (int)((W + WT - 1) / WT);
+  KArgs a;
+  a.out = enc;
+  a.ld_out = ld_enc;
+  a.W = (int)W;
+  a.n = (int)p->n;
+  a.k = (int)p->k;
+  a.L = L;
+  a.C = C;
+  a.twf = p->tenc.twf;
+  a.status = p->status;
+  TmaEncodeArgs t;
+  t.twc = p->twc;
+  t.rows_staged = rows_staged;
+  t.box_rows = box_rows;
+  t.grid = std::min(ntiles, p->sms);
+  t.map = &map;
+  if (launch_encode_tma(L, C, a, t, st) != 0) return 1;
+  return cuda_ok(cudaGetLastError());
+}
+
 static int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
+  const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
+  if (t != 1) return t;
   if (!p->split) {
     const TileOps& ops = tile_ops((int)p->n);
     KArgs a;
@@ -616,6 +691,32 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
     return code;
   };
   if (rc) return fail(rc);
+  {
+    const char* e = std::getenv("FNTRS_NO_TMA");
+    p->no_tma = e && e[0] == '1';
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->dev);
+    if (n >= 64 && n <= 4096) {
+      p->enc_L = (int)n;
+      p->enc_C = 1;
+    } else if (n == 8192 && k <= 4096) {
+      p->enc_L = 4096;
+      p->enc_C = 2;
+    }
+    if (p->enc_L && (rc = get_tables(p->enc_L, &p->tenc))) return fail(rc);
+    if (p->enc_C == 2) {
+      // twc[i2*R1 + q] = r_L^(i2 * bitrev(q)) * r_n^i2, i2 < L/R1
+      int r[3];
+      sched_radices(p->enc_L, r);
+      const int L = p->enc_L, R1 = r[0], S1 = L / R1, b0 = ilog2i(R1);
+      const uint32_t rL = default_root(L), rn = default_root(n);
+      std::vector<uint32_t> t((size_t)L);
+      for (int i2 = 0; i2 < S1; ++i2)
+        for (int q = 0; q < R1; ++q)
+          t[(size_t)i2 * R1 + q] =
+              hmul(hpow(rL, (uint64_t)i2 * bitrev_h(q, b0) % L), hpow(rn, (uint64_t)i2));
+      if ((rc = upload(&p->twc, t))) return fail(rc);
+    }
+  }
   if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess) return fail(FNT_RS_E_CUDA);
   if (cudaMemsetAsync(p->status, 0, sizeof(int), S(stream)) != cudaSuccess)
     return fail(FNT_RS_E_CUDA);
@@ -640,6 +741,7 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   cudaDeviceSynchronize();
   cudaFree(p->status);
   cudaFree(p->pscratch);
+  cudaFree(p->twc);
   for (auto& sl : p->slots) {
     cudaFree(sl.pat);
     cudaFree(sl.ahat);

@@ -49,6 +49,15 @@ void register_tile_ops_small();
 void register_tile_ops_mid();
 void register_tile_ops_big();
 
+// Persistent TMA-staged encode for tile length L (C = 1) or n = 2L (C = 2).
+// Returns -1 if the configuration has no instantiation.
+struct TmaEncodeArgs {
+  const uint32_t* twc;
+  int rows_staged, box_rows, grid;
+  const void* map;  // CUtensorMap*
+};
+int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
+
 // Split-transform passes (n = C * kLocalL).
 Launch local_launcher(bool inverse, int mode);
 Launch cross_launcher(int C, bool inverse, int load_mode);

@@ -8,12 +8,17 @@
 // applies the inter-pass twiddles and writes back in place.  Decimation in
 // frequency (DIF) reads natural order and leaves the spectrum in
 // digit-reversed "slot" order; the transposed decimation-in-time (DIT) pass
-// sequence reads slot order and produces natural order.  The data between
-// passes live in shared memory as [slot][codeword] u32 with an XOR swizzle of
-// the slot index that keeps every pass free of bank conflicts.
+// sequence reads slot order and produces natural order.
 //
 // Slot layout after DIF pass p:  slot = j1*S1 + j2*S2 + j3   (S3 = 1)
 // holds spectrum index          j    = j1 + R1*j2 + R1*R2*j3.
+//
+// Shared memory holds [slot][codeword] u32 with WT words of padding after
+// every block of RL slots (RL = radix of the last pass).  A warp touches
+// 32/WT consecutive slots of one block in every pass but the last, and 32/WT
+// consecutive blocks in the last; the padding staggers those blocks across
+// banks, and every per-register offset within a pass is a compile-time
+// constant.
 #pragma once
 #include "field.cuh"
 
@@ -44,16 +49,27 @@ struct Sched {
   }
 };
 
-// Shared-memory address of (slot, codeword c): swizzle the low bits of the
-// slot by the last-pass block index so that the 32/WT slot groups a warp
-// touches fall in different banks in every pass.
+// Padded shared-memory layout of one [L][WT] buffer.
 template <class S, int WT>
-__device__ __forceinline__ int sm_addr(int slot, int c) {
-  constexpr int G = (WT >= 32) ? 1 : (32 / WT);
-  constexpr int SW = ((G < S::RL) ? G : S::RL) - 1;
-  constexpr int LB = ilog2(S::RL);
-  const int phys = slot ^ ((slot >> LB) & SW);
-  return phys * WT + c;
+struct Lay {
+  static constexpr int PADW = WT < 32 ? WT : 0;
+  static constexpr int LB = ilog2(S::RL);
+  static constexpr int WORDS = S::L * WT + (S::L / S::RL) * PADW;
+  static __device__ __forceinline__ int addr(int slot, int c) {
+    return slot * WT + (slot >> LB) * PADW + c;
+  }
+  // pass 1: slot = q*S1 + i2
+  static constexpr int P1_STRIDE = S::S1 * WT + (S::S1 >> LB) * PADW;
+  // middle pass of 3: slot = b*S1 + q*S2 + i2 (S2 = RL)
+  static constexpr int MID_B = P1_STRIDE;
+  static constexpr int MID_STRIDE = S::S2 * WT + (S::S2 >> LB) * PADW;
+  // last pass: slot = b*RL + q
+  static constexpr int LAST_B = S::RL * WT + PADW;
+};
+
+template <class S, int WT>
+constexpr int smem_words() {
+  return S::NP >= 2 ? Lay<S, WT>::WORDS : 0;
 }
 
 // multiply register q by table entry q (table entry 0 is always 1: skipped)
@@ -96,6 +112,7 @@ __device__ __forceinline__ void bitrev_regs(uint32_t* x) {
 template <class S, int WT, int NT, bool INV, class Load, class Store>
 __device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restrict__ tw, Load& load,
                                           Store& store) {
+  using Y = Lay<S, WT>;
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, i2 = t / WT;
@@ -108,8 +125,9 @@ __device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restri
       for (int q = 0; q < R; ++q) store(bitrev(q, B), c, x[q]);
     } else {
       twiddle_regs<R>(x, tw + i2 * R);
+      uint32_t* base = sm + Y::addr(i2, c);
 #pragma unroll
-      for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)] = x[q];
+      for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
     }
   }
 }
@@ -117,18 +135,19 @@ __device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restri
 // DIF pass 2 of a 3-pass schedule, slots -> slots.
 template <class S, int WT, int NT, bool INV>
 __device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict__ tw2) {
+  using Y = Lay<S, WT>;
   constexpr int R = S::R2, SP = S::S2, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, g = t / WT;
     const int b = g / SP, i2 = g % SP;
-    const int base = b * S::S1 + i2;
+    uint32_t* base = sm + b * Y::MID_B + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(base + q * SP, c)];
+    for (int q = 0; q < R; ++q) x[q] = base[q * Y::MID_STRIDE];
     dft_reg<R, INV>(x);
     twiddle_regs<R>(x, tw2 + i2 * R);
 #pragma unroll
-    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)] = x[q];
+    for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::MID_STRIDE] = x[q];
   }
 }
 
@@ -136,16 +155,18 @@ __device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict
 template <class S, int WT, int NT, bool INV, class Store>
 __device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
   static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
   constexpr int R = S::RL, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
+    const uint32_t* base = sm + b * Y::LAST_B + c;
     uint32_t x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+    for (int q = 0; q < R; ++q) x[q] = base[q * WT];
     dft_reg<R, INV>(x);
-    const int base = S::natural(b * R);
+    const int j0 = S::natural(b * R);
 #pragma unroll
-    for (int q = 0; q < R; ++q) store(base + (S::L / R) * bitrev(q, B), c, x[q]);
+    for (int q = 0; q < R; ++q) store(j0 + (S::L / R) * bitrev(q, B), c, x[q]);
   }
 }
 
@@ -153,36 +174,38 @@ __device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
 template <class S, int WT, int NT, bool INV>
 __device__ __forceinline__ void dif_last_inplace(uint32_t* sm) {
   static_assert(S::NP >= 2, "");
-  constexpr int R = S::RL;
+  using Y = Lay<S, WT>;
+  constexpr int R = S::RL, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
+    uint32_t* base = sm + b * Y::LAST_B + c;
     uint32_t x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(b * R + q, c)];
+    for (int q = 0; q < R; ++q) x[q] = base[q * WT];
     dft_reg<R, INV>(x);
     // register q holds spectrum digit bitrev(q): slot b*R + bitrev(q)
-    bitrev_regs<R>(x);
 #pragma unroll
-    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + q, c)] = x[q];
+    for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
   }
 }
 
 // DIT pass 2 of a 3-pass schedule (transposed DIF pass 2), slots -> slots.
 template <class S, int WT, int NT, bool INV>
 __device__ __forceinline__ void dit_mid(uint32_t* sm, const uint32_t* __restrict__ tw2) {
+  using Y = Lay<S, WT>;
   constexpr int R = S::R2, SP = S::S2, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, g = t / WT;
     const int b = g / SP, i2 = g % SP;
-    const int base = b * S::S1 + i2;
+    uint32_t* base = sm + b * Y::MID_B + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)];
+    for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::MID_STRIDE];
     twiddle_regs<R>(x, tw2 + i2 * R);
     bitrev_regs<R>(x);
     dft_reg<R, INV>(x);
 #pragma unroll
-    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(base + bitrev(q, B) * SP, c)] = x[q];
+    for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::MID_STRIDE] = x[q];
   }
 }
 
@@ -192,12 +215,14 @@ template <class S, int WT, int NT, bool INV, class Store>
 __device__ __forceinline__ void dit_first(uint32_t* sm, const uint32_t* __restrict__ tw,
                                           Store& store) {
   static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, i2 = t / WT;
+    const uint32_t* base = sm + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = sm[sm_addr<S, WT>(bitrev(q, B) * SP + i2, c)];
+    for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
     twiddle_regs<R>(x, tw + i2 * R);
     bitrev_regs<R>(x);
     dft_reg<R, INV>(x);
@@ -211,18 +236,20 @@ __device__ __forceinline__ void dit_first(uint32_t* sm, const uint32_t* __restri
 template <class S, int WT, int NT, bool INV, bool MUL2>
 __device__ __forceinline__ void dit_last_inplace(uint32_t* sm, const uint32_t* sm2) {
   static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
   constexpr int R = S::RL, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
+    const int off = b * Y::LAST_B + c;
     uint32_t x[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int a = sm_addr<S, WT>(b * R + q, c);
+      const int a = off + q * WT;
       x[q] = MUL2 ? m_mul(sm[a], m_to_p(sm2[a])) : sm[a];
     }
     dft_reg<R, INV>(x);
 #pragma unroll
-    for (int q = 0; q < R; ++q) sm[sm_addr<S, WT>(b * R + bitrev(q, B), c)] = x[q];
+    for (int q = 0; q < R; ++q) sm[off + bitrev(q, B) * WT] = x[q];
   }
 }
 

@@ -66,6 +66,21 @@ def test_encode_split_sizes_sampled(pkg, n, k, W):
     assert np.array_equal(got[:, cols], oracle.encode(src[:, cols], n))
 
 
+@pytest.mark.parametrize("n,k,W", [(64, 40, 48), (512, 256, 72), (1024, 1000, 40),
+                                   (2048, 1024, 24), (4096, 4000, 16), (4096, 4096, 64),
+                                   (8192, 4096, 40), (8192, 3000, 24), (8192, 4096, 2048)])
+def test_encode_tma_and_fallback_paths(pkg, n, k, W, monkeypatch):
+    # aligned widths take the TMA-staged persistent kernel, FNTRS_NO_TMA the generic one
+    src = synth.source(5 * n + k + W, k, W)
+    cols = slice(None) if W <= 64 else [0, 1, W // 2, W - 1]
+    want = oracle.encode(np.ascontiguousarray(src[:, cols]), n)
+    got_tma = _enc(pkg, pkg.Plan(n, k), src)
+    monkeypatch.setenv("FNTRS_NO_TMA", "1")
+    got_gen = _enc(pkg, pkg.Plan(n, k), src)
+    assert np.array_equal(got_tma[:, cols], want)
+    assert np.array_equal(got_gen, got_tma)
+
+
 def test_encode_leading_dimensions(pkg):
     n, k, W = 1024, 512, 100
     src = synth.source(9, k, W)
