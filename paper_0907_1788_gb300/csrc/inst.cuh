@@ -125,3 +125,33 @@ int launch_encode_tma_t(const KArgs& a, const uint32_t* twc, int rows_staged, in
 }
 
 }  // namespace fntrs
+
+namespace fntrs {
+constexpr int decode_tma_max_rows(int L) { return L <= 256 ? L : L / 2; }
+
+template <class S, int WT, int NT>
+int launch_decode_tma_t(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  auto kern = k_decode_tma<S, WT, NT>;
+  constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
+  const int smem = work + t.rows_staged * WT * 4 + 16;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!done[dev & 63]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             work + decode_tma_max_rows(S::L) * WT * 4 + 16) != cudaSuccess)
+      return -1;
+    done[dev & 63] = true;
+  }
+  kern<<<t.grid, NT, smem, st>>>(a, t.pat32, t.rows_staged, t.box_rows,
+                                 *static_cast<const CUtensorMap*>(t.map));
+  count_launch();
+  return 0;
+}
+
+template <int L>
+int decode_tma_for(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  using S = typename SchedFor<L>::type;
+  return launch_decode_tma_t<S, wt_one(L), nt_for(L)>(a, t, st);
+}
+}  // namespace fntrs

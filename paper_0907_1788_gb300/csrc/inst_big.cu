@@ -19,3 +19,13 @@ int launch_encode_tma_big(int L, int C, const KArgs& a, const TmaEncodeArgs& t, 
   return -1;
 }
 }  // namespace fntrs
+
+namespace fntrs {
+int launch_decode_tma_big(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  switch (L) {
+    case 4096: return decode_tma_for<4096>(a, t, st);
+    case 8192: return decode_tma_for<8192>(a, t, st);
+    default: return -1;
+  }
+}
+}  // namespace fntrs

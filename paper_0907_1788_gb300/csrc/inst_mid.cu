@@ -26,3 +26,14 @@ int launch_encode_tma_mid(int L, int C, const KArgs& a, const TmaEncodeArgs& t, 
   }
 }
 }  // namespace fntrs
+
+namespace fntrs {
+int launch_decode_tma_mid(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  switch (L) {
+    case 512: return decode_tma_for<512>(a, t, st);
+    case 1024: return decode_tma_for<1024>(a, t, st);
+    case 2048: return decode_tma_for<2048>(a, t, st);
+    default: return -1;
+  }
+}
+}  // namespace fntrs

@@ -31,3 +31,14 @@ int launch_encode_tma_small(int L, int C, const KArgs& a, const TmaEncodeArgs& t
   }
 }
 }  // namespace fntrs
+
+namespace fntrs {
+int launch_decode_tma_small(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  switch (L) {
+    case 64: return decode_tma_for<64>(a, t, st);
+    case 128: return decode_tma_for<128>(a, t, st);
+    case 256: return decode_tma_for<256>(a, t, st);
+    default: return -1;
+  }
+}
+}  // namespace fntrs

@@ -511,6 +511,139 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Persistent fused decode with TMA-staged received rows (packed layout:
+// row i of recv holds the symbols of positions[i]; n = L, k <= n/2).  Same
+// transform sequence as k_decode; pass 1 gathers u[z] = v_row(z) * c_z from the
+// staged [k][WT] tile through pat32[z] = (row << 17) | c_z (c_z = 0: unused).
+// smem: work (Lay WORDS u32) | stage (rows_staged * WT u32) | mbarrier.
+// ---------------------------------------------------------------------------
+template <int WT>
+struct LoadStaged {
+  const uint32_t* stage;
+  const uint32_t* pat32;
+  uint32_t bad;
+  __device__ __forceinline__ uint32_t operator()(int z, int c) {
+    const uint32_t e = __ldg(pat32 + z);
+    const uint32_t w = e & 0x1FFFFu;
+    const uint32_t v = w ? stage[(e >> 17) * WT + c] : 0u;
+    bad |= v > 65536u ? 1u : 0u;
+    return m_mul(v, w);
+  }
+};
+
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
+                 const __grid_constant__ CUtensorMap trecv) {
+  static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
+  constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
+  extern __shared__ __align__(128) uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)rows_staged * WT);
+  const int ntiles = (a.W + WT - 1) / WT;
+  const int nbox = rows_staged / box_rows;
+  const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
+  const uint32_t* tw1f = a.twf;
+  const uint32_t* tw1i = a.twi;
+  const uint32_t* __restrict__ ahat = a.ahat;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+    mbar_expect_tx(bar, tx_bytes);
+    for (int bx = 0; bx < nbox; ++bx)
+      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, (int)blockIdx.x * WT,
+                  bx * box_rows, bar);
+  }
+  uint32_t parity = 0;
+  LoadStaged<WT> load{stage, pat32, 0u};
+  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  NopStore nop;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool ok = mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        mbar_wait(bar, parity);
+      }
+      return;
+    }
+    parity ^= 1u;
+    store.col0 = tile * WT;
+    // D1 pass 1 (root r^-1) from the stage
+    dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
+    __syncthreads();
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, tx_bytes);
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, (tile + (int)gridDim.x) * WT,
+                    bx * box_rows, bar);
+    }
+    if constexpr (S::NP == 3) {
+      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+      __syncthreads();
+    }
+    // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
+    {
+      constexpr int R = S::RL, B = ilog2(R);
+      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+        const int c = t % WT, b = t / WT;
+        uint32_t* base = sm + b * Y::LAST_B + c;
+        uint32_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = base[q * WT];
+        dft_reg<R, true>(x);
+        const int j0 = S::natural(b * R);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
+        bitrev_regs<R>(x);
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
+      }
+    }
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
+      __syncthreads();
+    }
+    // last D2 pass * ahat + first D3 pass
+    {
+      constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+        const int c = t % WT, i2 = t / WT;
+        uint32_t* base = sm + Y::addr(i2, c);
+        uint32_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
+        twiddle_regs<R>(x, tw1f + i2 * R);
+        bitrev_regs<R>(x);
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
+        bitrev_regs<R>(x);
+        dft_reg<R, true>(x);
+        twiddle_regs<R>(x, tw1i + i2 * R);
+#pragma unroll
+        for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
+      }
+    }
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+      __syncthreads();
+    }
+    dif_last<S, WT, NT, true>(sm, store);
+    __syncthreads();
+  }
+  if (load.bad) atomicOr(a.status, ST_RANGE);
+  store.flush();
+}
+
+// ---------------------------------------------------------------------------
 // Fused decode for n = L and k > n/2: the truncated product of step 6 is
 // split at h = n/2 so that only length-n cyclic products occur:
 //   P mod x^k = A0 S0 + x^h (A0 S1 + A1 S0),  A = A0 + x^h A1, S = S0 + x^h S1.

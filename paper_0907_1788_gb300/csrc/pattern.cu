@@ -1,4 +1,6 @@
-// Per-erasure-pattern preparation on the device (Sec. II.B, steps 1-3):
+// Per-erasure-pattern preparation on the device (Sec. II.B, steps 1-3).
+// Two routes compute the same tables: the log-domain correlation below
+// (default: a handful of batched FNTs) and the paper's product tree:
 //   step 1  A(x) = prod_{i<k} (x - r^(z_i)) by a product tree: leaves are
 //           multiplied 32 at a time in registers, then pairs of nodes with
 //           FNT products level by level ("M(n) = 3 FNTs");
@@ -130,11 +132,148 @@ __global__ void k_pat_final(const uint32_t* __restrict__ E, int ncols, const uin
   }
 }
 
+// ---------------------------------------------------------------------------
+// Log-domain pattern build.  With g[d] = log_3(1 - r^d) (d != 0), g[0] = 0 and
+// S(j) = sum_{z in R} g[z - j] (a cyclic correlation of the indicator 1_R):
+//   j not received:  log A(r^j)  = j*k*(65536/n)     + S(j)   (mod 65536)
+//   j received:      log A'(r^j) = j*(k-1)*(65536/n) + S(j)
+// because r^j - r^z = r^j (1 - r^(z-j)).  S is computed exactly as a sum of
+// D digit-wise cyclic convolutions over F_p (each digit < 2^b with
+// k (2^b - 1) < p, so no convolution value wraps).
+// ---------------------------------------------------------------------------
+
+__global__ void k_lg_init(uint2* pat, uint32_t* ind, int n) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n) {
+    pat[z] = make_uint2(0xFFFFFFFFu, 0u);
+    ind[z] = 0u;
+  }
+}
+
+__global__ void k_lg_scatter(const uint32_t* __restrict__ pos, int k, uint2* pat, uint32_t* ind) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) {
+    const uint32_t z = pos[i];
+    ind[z] = 1u;
+    pat[z].x = (uint32_t)i;
+  }
+}
+
+// P[j][t] = spec[j] * Ghat[j][t]
+__global__ void k_lg_mul(const uint32_t* __restrict__ spec, const uint32_t* __restrict__ ghat,
+                         int D, int n, uint32_t* __restrict__ P) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * D) return;
+  const int j = (int)(t / D);
+  P[t] = m_to_p(m_mul(ghat[t], m_to_p(spec[j])));
+}
+
+// weights of received positions; A(r^j) of the others (Aval) and, unless the
+// step-6 product is split, ahat_j = n^-1 (A(r^j) - r^(jk)) = n^-1 FNT(A mod x^k)_j.
+__global__ void k_lg_final(const uint32_t* __restrict__ conv, int D, int b, int n, int k,
+                           const uint32_t* __restrict__ exp3, uint32_t ninv, uint2* pat,
+                           uint32_t* __restrict__ pat32, uint32_t* __restrict__ aval,
+                           uint32_t* __restrict__ ahat) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  uint32_t S = 0u;
+  for (int t = 0; t < D; ++t) S += conv[(size_t)j * D + t] << (b * t);
+  const uint32_t step = 65536u / (uint32_t)n;
+  const uint32_t jl = (uint32_t)j * step;  // log_3 r^j
+  const bool received = pat[j].x != 0xFFFFFFFFu;
+  uint32_t A = 0u;
+  if (received) {
+    const uint32_t ld = (jl * (uint32_t)(k - 1) + S) & 0xFFFFu;  // log A'(r^j)
+    // c = -r^-j / A'(r^j) = -3^-(jl + ld)
+    const uint32_t e = (0u - (jl + ld)) & 0xFFFFu;
+    const uint32_t c = kP - exp3[e];
+    pat[j].y = c;
+    pat32[j] = (pat[j].x << 17) | c;
+  } else {
+    pat32[j] = 0u;
+    A = exp3[(jl * (uint32_t)k + S) & 0xFFFFu];
+  }
+  if (aval) aval[j] = A;
+  if (ahat) {
+    const uint32_t rjk = exp3[(jl * (uint32_t)k) & 0xFFFFu];
+    ahat[j] = p_mul(m_to_p(m_sub(A, rjk)), ninv);
+  }
+}
+
+// coefficient halves of A (k > n/2): M[j][0] = A_j (j < h), M[j][1] = A_(h+j) (j < k-h);
+// k = n means A = x^n - 1, A mod x^n = -1.
+__global__ void k_lg_halves(const uint32_t* __restrict__ coef, int n, int k, uint32_t* M) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int h = n / 2;
+  uint32_t a0 = 0u, a1 = 0u;
+  if (k == n) {
+    a0 = j == 0 ? kP - 1u : 0u;
+  } else {
+    if (j < h) a0 = coef[j];
+    if (j < k - h) a1 = coef[h + j];
+  }
+  M[(size_t)j * 2] = a0;
+  M[(size_t)j * 2 + 1] = a1;
+}
+
+__global__ void k_lg_scale2(const uint32_t* __restrict__ E, int n, uint32_t ninv,
+                            uint32_t* __restrict__ ahat, uint32_t* __restrict__ ahat2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  ahat[j] = p_mul(E[(size_t)j * 2], ninv);
+  ahat2[j] = p_mul(E[(size_t)j * 2 + 1], ninv);
+}
+
+// compact per-position entry (row << 17) | weight for the staged decode
+__global__ void k_pat32(const uint2* __restrict__ pat, uint32_t* __restrict__ pat32, int n) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n) {
+    const uint2 e = pat[z];
+    pat32[z] = e.y ? ((e.x << 17) | e.y) : 0u;
+  }
+}
+
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
 
-void launch_pat_init(uint2* pat, int n, cudaStream_t st) {
+void launch_pat32(const uint2* pat, uint32_t* pat32, int n, cudaStream_t st) {
+  k_pat32<<<blocks_for(n, 256), 256, 0, st>>>(pat, pat32, n);
+  count_launch();
+}
+
+void launch_lg_init(uint2* pat, uint32_t* ind, int n, cudaStream_t st) {
+  k_lg_init<<<blocks_for(n, 256), 256, 0, st>>>(pat, ind, n);
+  count_launch();
+}
+void launch_lg_scatter(const uint32_t* pos, int k, uint2* pat, uint32_t* ind, cudaStream_t st) {
+  k_lg_scatter<<<blocks_for(k, 256), 256, 0, st>>>(pos, k, pat, ind);
+  count_launch();
+}
+void launch_lg_mul(const uint32_t* spec, const uint32_t* ghat, int D, int n, uint32_t* P,
+                   cudaStream_t st) {
+  k_lg_mul<<<blocks_for((long long)n * D, 256), 256, 0, st>>>(spec, ghat, D, n, P);
+  count_launch();
+}
+void launch_lg_final(const uint32_t* conv, int D, int b, int n, int k, const uint32_t* exp3,
+                     uint32_t ninv, uint2* pat, uint32_t* pat32, uint32_t* aval, uint32_t* ahat,
+                     cudaStream_t st) {
+  k_lg_final<<<blocks_for(n, 256), 256, 0, st>>>(conv, D, b, n, k, exp3, ninv, pat, pat32, aval,
+                                                  ahat);
+  count_launch();
+}
+void launch_lg_halves(const uint32_t* coef, int n, int k, uint32_t* M, cudaStream_t st) {
+  k_lg_halves<<<blocks_for(n, 256), 256, 0, st>>>(coef, n, k, M);
+  count_launch();
+}
+void launch_lg_scale2(const uint32_t* E, int n, uint32_t ninv, uint32_t* ahat, uint32_t* ahat2,
+                      cudaStream_t st) {
+  k_lg_scale2<<<blocks_for(n, 256), 256, 0, st>>>(E, n, ninv, ahat, ahat2);
+  count_launch();
+}
+
+void launch_pat_init(uint2* pat, int n, cudaStream_t st) {  // product-tree route
   k_pat_init<<<blocks_for(n, 256), 256, 0, st>>>(pat, n);
   count_launch();
 }

@@ -54,6 +54,16 @@ int launch_encode_tma_small(int L, int C, const KArgs& a, const TmaEncodeArgs& t
 int launch_encode_tma_mid(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 int launch_encode_tma_big(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 
+int launch_decode_tma_small(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
+int launch_decode_tma_mid(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
+int launch_decode_tma_big(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
+
+int launch_decode_tma(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  if (L <= 256) return launch_decode_tma_small(L, a, t, st);
+  if (L <= 2048) return launch_decode_tma_mid(L, a, t, st);
+  return launch_decode_tma_big(L, a, t, st);
+}
+
 int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st) {
   if (L <= 256) return launch_encode_tma_small(L, C, a, t, st);
   if (L <= 2048) return launch_encode_tma_mid(L, C, a, t, st);
@@ -75,6 +85,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
   return fn;
 }
 
+void launch_lg_init(uint2* pat, uint32_t* ind, int n, cudaStream_t st);
+void launch_lg_scatter(const uint32_t* pos, int k, uint2* pat, uint32_t* ind, cudaStream_t st);
+void launch_lg_mul(const uint32_t* spec, const uint32_t* ghat, int D, int n, uint32_t* P,
+                   cudaStream_t st);
+void launch_lg_final(const uint32_t* conv, int D, int b, int n, int k, const uint32_t* exp3,
+                     uint32_t ninv, uint2* pat, uint32_t* pat32, uint32_t* aval, uint32_t* ahat,
+                     cudaStream_t st);
+void launch_pat32(const uint2* pat, uint32_t* pat32, int n, cudaStream_t st);
+void launch_lg_halves(const uint32_t* coef, int n, int k, uint32_t* M, cudaStream_t st);
+void launch_lg_scale2(const uint32_t* E, int n, uint32_t ninv, uint32_t* ahat, uint32_t* ahat2,
+                      cudaStream_t st);
 void launch_pat_init(uint2* pat, int n, cudaStream_t st);
 void launch_leaves(const uint32_t* pos, int k, const uint32_t* powf, uint32_t* out, int nodes,
                    cudaStream_t st);
@@ -190,6 +211,33 @@ static int get_tables(int L, Tables* out) {
   return FNT_RS_OK;
 }
 
+// 3^e mod p for e < 65536 (3 is a primitive root, Sec. II.A), one table per device.
+static std::mutex g_exp_mu;
+static std::map<int, uint32_t*> g_exp3;
+
+static int get_exp3(uint32_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FNT_RS_E_CUDA;
+  std::lock_guard<std::mutex> lk(g_exp_mu);
+  auto it = g_exp3.find(dev);
+  if (it != g_exp3.end()) {
+    *out = it->second;
+    return FNT_RS_OK;
+  }
+  std::vector<uint32_t> t(65536);
+  uint32_t x = 1;
+  for (int e = 0; e < 65536; ++e) {
+    t[e] = x;
+    x = hmul(x, 3);
+  }
+  uint32_t* d = nullptr;
+  int rc = upload(&d, t);
+  if (rc) return rc;
+  g_exp3[dev] = d;
+  *out = d;
+  return FNT_RS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
@@ -200,6 +248,7 @@ struct PatternSlot {
   uint2* pat = nullptr;
   uint32_t* ahat = nullptr;
   uint32_t* ahat2 = nullptr;
+  uint32_t* pat32 = nullptr;  // (row << 17) | weight per position
   uint32_t* pos_d = nullptr;  // first k positions (device)
   uint32_t* pos_h = nullptr;  // pinned staging of the upload
   cudaEvent_t staged = nullptr;  // recorded after the upload
@@ -224,6 +273,11 @@ struct fnt_rs_plan_s {
   Tables tl;             // tables of the local length (split only)
   Tables tenc;           // schedule tables of the TMA encode's tile length
   uint32_t* twc = nullptr;  // TMA encode, class 1 of n = 2L: pass-1 twiddles times r_n^i2
+  // log-domain pattern build: digits of g[d] = log_3(1 - r^d), b bits each
+  bool plan_tree = false;   // use the product tree instead
+  int lg_b = 4, lg_D = 4;
+  uint32_t* ghat = nullptr;  // [n][D] transforms of the reversed digit vectors
+  uint32_t* exp3 = nullptr;  // shared table
   int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
   bool no_tma = false;
   int sms = 1;
@@ -319,12 +373,46 @@ static int run_fnt_default(int L, const uint32_t* in, size_t ld_in, uint32_t* ou
 // pattern build (steps 1-3) into slot `si`
 // ---------------------------------------------------------------------------
 static size_t pattern_scratch_words(uint32_t n, uint32_t k) {
-  // level ping-pong, [n][3] matrix + transform, big-level matrices + work
+  // product tree: level ping-pong, [n][3] matrix + transform, big-level matrices + work
   size_t K2 = 1;
   while (K2 < k) K2 <<= 1;
   const size_t lvl = 4 * (size_t)k + 4 * 64 + 2 * K2 + 64;
   const size_t big = (K2 > (size_t)kTileMaxL / 2) ? 8 * (size_t)(2 * K2) + 8 * K2 : 0;
-  return 2 * lvl + 9 * (size_t)n + big + 1024;
+  const size_t tree = 2 * lvl + 9 * (size_t)n + big + 1024;
+  // log route: ind, spec, aval, coef (n each), M2, E2 (2n each), P, conv, work (n*16 each)
+  const size_t lg = 8 * (size_t)n + 3 * 16 * (size_t)n + 1024;
+  return std::max(tree, lg);
+}
+
+// Log-domain build of the pattern tables (see pattern.cu).
+static int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
+  const int n = (int)p->n, k = (int)p->k, D = p->lg_D;
+  uint32_t* ind = p->pscratch;
+  uint32_t* spec = ind + n;
+  uint32_t* aval = spec + n;
+  uint32_t* coef = aval + n;
+  uint32_t* M2 = coef + n;
+  uint32_t* E2 = M2 + 2 * (size_t)n;
+  uint32_t* P = E2 + 2 * (size_t)n;
+  uint32_t* conv = P + 16 * (size_t)n;
+  uint32_t* work = conv + 16 * (size_t)n;
+  int rc;
+  launch_lg_init(sl.pat, ind, n, st);
+  launch_lg_scatter(sl.pos_d, k, sl.pat, ind, st);
+  if ((rc = run_fnt_default(n, ind, 1, spec, 1, 1, false, 1, work, st))) return rc;
+  launch_lg_mul(spec, p->ghat, D, n, P, st);
+  if ((rc = run_fnt_default(n, P, D, conv, D, D, true, 1, work, st))) return rc;
+  if (!p->blocked) {
+    launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, nullptr, sl.ahat,
+                    st);
+    return cuda_ok(cudaGetLastError());
+  }
+  launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, aval, nullptr, st);
+  if ((rc = run_fnt_default(n, aval, 1, coef, 1, 1, true, 1, work, st))) return rc;
+  launch_lg_halves(coef, n, k, M2, st);
+  if ((rc = run_fnt_default(n, M2, 2, E2, 2, 2, false, 1, work, st))) return rc;
+  launch_lg_scale2(E2, n, p->ninv, sl.ahat, sl.ahat2, st);
+  return cuda_ok(cudaGetLastError());
 }
 
 static int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
@@ -384,6 +472,7 @@ static int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   launch_pat_prep(lv[cur], k, n, ncols, n / 2, M, st);
   if ((rc = run_fnt_default(n, M, ncols, E, ncols, ncols, false, 1, work, st))) return rc;
   launch_pat_final(E, ncols, sl.pos_d, k, n, p->tn.powi, p->ninv, sl.pat, sl.ahat, sl.ahat2, st);
+  launch_pat32(sl.pat, sl.pat32, n, st);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -427,7 +516,7 @@ static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, c
   if ((rc = cuda_ok(cudaMemcpyAsync(sl.pos_d, sl.pos_h, key.size() * 4, cudaMemcpyHostToDevice, st))))
     return rc;
   if ((rc = cuda_ok(cudaEventRecord(sl.staged, st)))) return rc;
-  if ((rc = build_pattern(p, sl, st))) return rc;
+  if ((rc = p->plan_tree ? build_pattern(p, sl, st) : build_pattern_log(p, sl, st))) return rc;
   sl.key.swap(key);
   sl.valid = true;
   sl.last_use = p->clock;
@@ -533,8 +622,57 @@ static int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint3
   return cuda_ok(cudaGetLastError());
 }
 
+// Persistent TMA-staged decode (packed rows, n <= tile limit, k <= n/2);
+// returns 1 if not applicable.
+static int decode_tma(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, uint16_t* out,
+                      size_t ld_out, size_t W, cudaStream_t st) {
+  if (p->no_tma || p->split || p->blocked || p->n < 64) return 1;
+  if ((reinterpret_cast<uintptr_t>(recv) % 16) != 0 || (ld_recv * 4) % 16 != 0) return 1;
+  auto fn = tmap_encode_fn();
+  if (!fn) return 1;
+  const int L = (int)p->n;
+  const TileOps& ops = tile_ops(L);
+  const int WT = ops.wt1;
+  const int box_rows = std::min(256, L);
+  const int rows_staged = (int)((p->k + box_rows - 1) / box_rows) * box_rows;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)p->k};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld_recv * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)WT, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(recv), dims, strides, box,
+         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 1;
+  const PatternSlot& sl = p->slots[p->current];
+  KArgs a;
+  a.out = out;
+  a.ld_out = ld_out;
+  a.W = (int)W;
+  a.n = L;
+  a.k = (int)p->k;
+  a.L = L;
+  a.C = 1;
+  a.twf = p->tn.twf;
+  a.twi = p->tn.twi;
+  a.ahat = sl.ahat;
+  a.status = p->status;
+  TmaDecodeArgs t;
+  t.pat32 = sl.pat32;
+  t.rows_staged = rows_staged;
+  t.box_rows = box_rows;
+  t.grid = std::min((int)((W + WT - 1) / WT), p->sms);
+  t.map = &map;
+  if (launch_decode_tma(L, a, t, st) != 0) return 1;
+  return cuda_ok(cudaGetLastError());
+}
+
 static int do_decode(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, uint16_t* out,
                      size_t ld_out, size_t W, void* workspace, cudaStream_t st, int slots) {
+  if (!slots) {
+    const int t = decode_tma(p, recv, ld_recv, out, ld_out, W, st);
+    if (t != 1) return t;
+  }
   const PatternSlot& sl = p->slots[p->current];
   KArgs a;
   a.slots = slots;
@@ -703,6 +841,45 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
       p->enc_C = 2;
     }
     if (p->enc_L && (rc = get_tables(p->enc_L, &p->tenc))) return fail(rc);
+    const char* pe = std::getenv("FNTRS_PLAN");
+    p->plan_tree = pe && std::strcmp(pe, "tree") == 0;
+    if ((rc = get_exp3(&p->exp3))) return fail(rc);
+    // digit width b with k (2^b - 1) < p: every digit convolution stays below p
+    p->lg_b = 15u * k < FNT_RS_P ? 4 : (7u * k < FNT_RS_P ? 3 : (3u * k < FNT_RS_P ? 2 : 1));
+    p->lg_D = (16 + p->lg_b - 1) / p->lg_b;
+    {
+      const int D = p->lg_D, b = p->lg_b;
+      std::vector<uint32_t> dl(65537, 0);
+      uint32_t x = 1;
+      for (uint32_t e = 0; e < 65536; ++e) {
+        dl[x] = e;
+        x = hmul(x, 3);
+      }
+      const uint32_t r = default_root(n);
+      std::vector<uint32_t> g(n, 0), dig((size_t)n * D);
+      uint32_t rd = r;
+      for (uint32_t d = 1; d < n; ++d) {
+        g[d] = dl[(1u + FNT_RS_P - rd) % FNT_RS_P];
+        rd = hmul(rd, r);
+      }
+      for (uint32_t d = 0; d < n; ++d) {
+        const uint32_t gr = g[(n - d) & (n - 1)];  // reversed: correlation as convolution
+        for (int t = 0; t < D; ++t) dig[(size_t)d * D + t] = (gr >> (b * t)) & ((1u << b) - 1u);
+      }
+      uint32_t *din = nullptr, *wk = nullptr;
+      if ((rc = upload(&din, dig))) return fail(rc);
+      if (cudaMalloc(&p->ghat, dig.size() * 4) != cudaSuccess ||
+          cudaMalloc(&wk, dig.size() * 4) != cudaSuccess) {
+        cudaFree(din);
+        cudaFree(wk);
+        return fail(FNT_RS_E_CUDA);
+      }
+      rc = run_fnt_default((int)n, din, D, p->ghat, D, D, false, 1, wk, S(stream));
+      if (!rc) rc = cuda_ok(cudaStreamSynchronize(S(stream)));
+      cudaFree(din);
+      cudaFree(wk);
+      if (rc) return fail(rc);
+    }
     if (p->enc_C == 2) {
       // twc[i2*R1 + q] = r_L^(i2 * bitrev(q)) * r_n^i2, i2 < L/R1
       int r[3];
@@ -727,6 +904,7 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
         cudaMalloc(&sl.ahat, (size_t)n * 4) != cudaSuccess ||
         cudaMalloc(&sl.ahat2, (size_t)n * 4) != cudaSuccess ||
         cudaMalloc(&sl.pos_d, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&sl.pat32, (size_t)n * 4) != cudaSuccess ||
         cudaMallocHost(&sl.pos_h, (size_t)n * 4) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.staged, cudaEventDisableTiming) != cudaSuccess)
       return fail(FNT_RS_E_CUDA);
@@ -742,11 +920,13 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   cudaFree(p->status);
   cudaFree(p->pscratch);
   cudaFree(p->twc);
+  cudaFree(p->ghat);
   for (auto& sl : p->slots) {
     cudaFree(sl.pat);
     cudaFree(sl.ahat);
     cudaFree(sl.ahat2);
     cudaFree(sl.pos_d);
+    cudaFree(sl.pat32);
     if (sl.pos_h) cudaFreeHost(sl.pos_h);
     if (sl.staged) cudaEventDestroy(sl.staged);
   }

@@ -58,6 +58,14 @@ struct TmaEncodeArgs {
 };
 int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 
+// Persistent TMA-staged decode (n = L <= tile limit, k <= n/2, packed rows).
+struct TmaDecodeArgs {
+  const uint32_t* pat32;
+  int rows_staged, box_rows, grid;
+  const void* map;  // CUtensorMap*
+};
+int launch_decode_tma(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
+
 // Split-transform passes (n = C * kLocalL).
 Launch local_launcher(bool inverse, int mode);
 Launch cross_launcher(int C, bool inverse, int load_mode);

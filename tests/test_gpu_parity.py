@@ -190,6 +190,31 @@ def test_roundtrip_every_codeword(pkg, n, k, W):
     assert plan.status() == 0
 
 
+@pytest.mark.parametrize("n,k,W", [(64, 32, 36), (256, 100, 68), (1024, 512, 40),
+                                   (2048, 1024, 20), (4096, 2048, 24), (8192, 4096, 12),
+                                   (8192, 4096, 2048), (8192, 6000, 8), (16384, 8192, 8)])
+@pytest.mark.parametrize("route", ["log", "tree"])
+def test_decode_paths_and_plan_routes(pkg, n, k, W, route, monkeypatch):
+    # plan tables by the log-domain correlation (default) or the product tree;
+    # aligned widths take the TMA-staged persistent decode, FNTRS_NO_TMA the generic one
+    if route == "tree":
+        monkeypatch.setenv("FNTRS_PLAN", "tree")
+    seed = 11 * n + k + W
+    src = synth.source(seed, k, W)
+    pos = synth.received_positions(n, synth.erased_uniform(seed + 1, n, k))
+    plan = pkg.Plan(n, k)
+    enc_h = _enc(pkg, plan, src)
+    assert np.array_equal(_dec(pkg, plan, enc_h[pos], pos), src)
+    v = synth.received_uniform(seed + 2, k, W)
+    got = _dec(pkg, plan, v, pos)
+    cols = slice(None) if W <= 64 else [0, 1, W - 2, W - 1]
+    want, _ = oracle.decode(np.ascontiguousarray(v[:, cols]), pos, n, k)
+    assert np.array_equal(got[:, cols], want)
+    monkeypatch.setenv("FNTRS_NO_TMA", "1")
+    plan2 = pkg.Plan(n, k)
+    assert np.array_equal(_dec(pkg, plan2, v, pos), got)
+
+
 def test_extra_positions_use_first_k(pkg):
     n, k, W = 256, 100, 30
     src = synth.source(44, k, W)
