@@ -47,9 +47,11 @@ __device__ __forceinline__ uint32_t m_rot_rt(uint32_t x, uint32_t s) {
   return __funnelshift_l(x, x, s & 31u);
 }
 
-// x * w in Z/M for any 32-bit x and w < 2^17
+// x * w in Z/M for any 32-bit x and w < 2^17: one 32x32->64 multiply, then
+// the high word folded onto the low one (2^32 = 1 in Z/M)
 __device__ __forceinline__ uint32_t m_mul(uint32_t x, uint32_t w) {
-  return m_add(x * w, __umulhi(x, w));
+  const uint64_t prod = (uint64_t)x * w;
+  return m_add((uint32_t)prod, (uint32_t)(prod >> 32));
 }
 
 // Reduce an element of Z/M to its representative in [0, p) = [0, 65536]:

@@ -22,8 +22,8 @@ template <> struct SchedFor<4096> { using type = Sched<4096, 16, 16, 16>; };
 template <> struct SchedFor<8192> { using type = Sched<8192, 32, 16, 16>; };
 
 // Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
-template <class Tag>
-inline void ensure_smem(void (*kern)(KArgs), int bytes) {
+template <class Tag, class F>
+inline void ensure_smem(F* kern, int bytes) {
   static bool done[64] = {};
   if (bytes <= 48 * 1024) return;
   int dev = 0;
@@ -79,6 +79,27 @@ void launch_poly_level(const KArgs& a, int, cudaStream_t st) {
   count_launch();
 }
 
+template <class S, int NT>
+void launch_plan_spec(const KArgs& a, const uint32_t* pos, uint32_t* spec, cudaStream_t st) {
+  auto kern = k_plan_spec<S, NT>;
+  const int smem = (Lay<S, 1>::WORDS + S::L) * 4;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  kern<<<1, NT, smem, st>>>(a, pos, spec);
+  count_launch();
+}
+
+template <class S, int NT>
+void launch_plan_conv(const KArgs& a, const uint32_t* spec, const uint32_t* ghat, int D,
+                      uint32_t* conv, cudaStream_t st) {
+  auto kern = k_plan_conv<S, NT>;
+  const int smem = smem_words<S, 1>() * 4;
+  struct Tag {};
+  ensure_smem<Tag>(kern, smem);
+  kern<<<D, NT, smem, st>>>(a, spec, ghat, D, conv);
+  count_launch();
+}
+
 template <int L>
 TileOps make_tile_ops() {
   using S = typename SchedFor<L>::type;
@@ -94,6 +115,10 @@ TileOps make_tile_ops() {
   ops.decode = &launch_decode<S, W1, NT>;
   ops.decode_split = &launch_decode_split<S, W2, NT>;
   if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;
+  if constexpr (L >= 64) {
+    ops.plan_spec = &launch_plan_spec<S, 512>;
+    ops.plan_conv = &launch_plan_conv<S, 512>;
+  }
   return ops;
 }
 

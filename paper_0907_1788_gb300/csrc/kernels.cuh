@@ -122,10 +122,11 @@ struct StoreRows32 {
   }
 };
 
-// Reduce to [0, p); 65536 (no 16-bit symbol) becomes 0 and sets `bad`.
+// Reduce to [0, p); 65536 (no 16-bit symbol) becomes 0 and raises `bad`
+// (a running maximum: bad ends at 65536 iff one value was out of range).
 __device__ __forceinline__ uint16_t to_symbol(uint32_t v, uint32_t& bad) {
   const uint32_t r = m_to_p(v);
-  bad |= r >> 16;
+  bad = max(bad, r);
   return (uint16_t)r;
 }
 
@@ -176,7 +177,7 @@ struct StoreLocal {
     }
   }
   __device__ __forceinline__ void flush() const {
-    if (bad) atomicOr(a.status, ST_RANGE);
+    if (bad > 65535u) atomicOr(a.status, ST_RANGE);
   }
 };
 
@@ -407,7 +408,7 @@ struct StoreOut16 {
     out[(size_t)j * ld + col] = to_symbol(v, bad);
   }
   __device__ __forceinline__ void flush() const {
-    if (bad) atomicOr(status, ST_RANGE);
+    if (bad > 65535u) atomicOr(status, ST_RANGE);
   }
 };
 
@@ -521,13 +522,13 @@ template <int WT>
 struct LoadStaged {
   const uint32_t* stage;
   const uint32_t* pat32;
-  uint32_t bad;
+  uint32_t vmax;  // largest received value seen (> 65536 is out of range)
+  // unused positions have weight 0 and row 0: the product vanishes, no branch
   __device__ __forceinline__ uint32_t operator()(int z, int c) {
     const uint32_t e = __ldg(pat32 + z);
-    const uint32_t w = e & 0x1FFFFu;
-    const uint32_t v = w ? stage[(e >> 17) * WT + c] : 0u;
-    bad |= v > 65536u ? 1u : 0u;
-    return m_mul(v, w);
+    const uint32_t v = stage[(e >> 17) * WT + c];
+    vmax = max(vmax, v);
+    return m_mul(v, e & 0x1FFFFu);
   }
 };
 
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(NT, 1)
     dif_last<S, WT, NT, true>(sm, store);
     __syncthreads();
   }
-  if (load.bad) atomicOr(a.status, ST_RANGE);
+  if (load.vmax > 65536u) atomicOr(a.status, ST_RANGE);
   store.flush();
 }
 
@@ -824,7 +825,7 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
     }
   }
   load.flush();
-  if (bad) atomicOr(a.status, ST_RANGE);
+  if (bad > 65535u) atomicOr(a.status, ST_RANGE);
 }
 
 template <class S, int WT, int NT>
@@ -833,6 +834,87 @@ __global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
     decode_split_regs<S::L, WT, NT>(a);
   } else {
     decode_split_smem<S, WT, NT>(a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Log-domain pattern build for n = L <= tile limit (see pattern.cu for the
+// identities).  k_plan_spec: one CTA resets the position table, scatters the
+// first k positions (their received-row index and the indicator 1_R) and
+// writes spec = FNT_n(1_R).  k_plan_conv: CTA t multiplies spec by the
+// transform of digit t of the reversed log table and writes its inverse FNT,
+// conv[j][t] = (1_R * g'_t)[j], exact integers below p.
+// smem: work (Lay<S,1> WORDS) | indicator (L words).
+// ---------------------------------------------------------------------------
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_plan_spec(KArgs a, const uint32_t* __restrict__ pos,
+                                                  uint32_t* __restrict__ spec) {
+  using Y = Lay<S, 1>;
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* ind = sm + Y::WORDS;
+  uint2* pat = const_cast<uint2*>(a.pat);
+  for (int z = threadIdx.x; z < S::L; z += NT) {
+    ind[z] = 0u;
+    pat[z] = make_uint2(0xFFFFFFFFu, 0u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.k; i += NT) {
+    const uint32_t z = pos[i];
+    ind[z] = 1u;
+    pat[z].x = (uint32_t)i;
+  }
+  __syncthreads();
+  struct LoadInd {
+    const uint32_t* ind;
+    __device__ uint32_t operator()(int i, int) const { return ind[i]; }
+  } ld{ind};
+  struct StoreSpec {
+    uint32_t* spec;
+    __device__ void operator()(int j, int, uint32_t v) const { spec[j] = m_to_p(v); }
+  } st{spec};
+  dif_first<S, 1, NT, false>(sm, a.twf, ld, st);
+  if constexpr (S::NP >= 2) {
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, 1, NT, false>(sm, a.twf + S::TW2_OFF);
+      __syncthreads();
+    }
+    dif_last<S, 1, NT, false>(sm, st);
+  }
+}
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_plan_conv(KArgs a, const uint32_t* __restrict__ spec,
+                                                  const uint32_t* __restrict__ ghat, int D,
+                                                  uint32_t* __restrict__ conv) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  const int t = blockIdx.x;
+  struct LoadProd {
+    const uint32_t* spec;
+    const uint32_t* ghat;
+    int D, t;
+    __device__ uint32_t operator()(int j, int) const {
+      return m_mul(__ldg(ghat + (size_t)j * D + t), __ldg(spec + j));
+    }
+  } ld{spec, ghat, D, t};
+  struct StoreConv {
+    uint32_t* conv;
+    int D, t;
+    uint32_t ninv;
+    __device__ void operator()(int j, int, uint32_t v) const {
+      conv[(size_t)j * D + t] = m_to_p(m_mul(v, ninv));
+    }
+  } st{conv, D, t, a.scale};
+  dif_first<S, 1, NT, true>(sm, a.twi, ld, st);
+  if constexpr (S::NP >= 2) {
+    __syncthreads();
+    if constexpr (S::NP == 3) {
+      dif_mid<S, 1, NT, true>(sm, a.twi + S::TW2_OFF);
+      __syncthreads();
+    }
+    dif_last<S, 1, NT, true>(sm, st);
   }
 }
 

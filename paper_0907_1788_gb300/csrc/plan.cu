@@ -397,11 +397,26 @@ static int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st)
   uint32_t* conv = P + 16 * (size_t)n;
   uint32_t* work = conv + 16 * (size_t)n;
   int rc;
-  launch_lg_init(sl.pat, ind, n, st);
-  launch_lg_scatter(sl.pos_d, k, sl.pat, ind, st);
-  if ((rc = run_fnt_default(n, ind, 1, spec, 1, 1, false, 1, work, st))) return rc;
-  launch_lg_mul(spec, p->ghat, D, n, P, st);
-  if ((rc = run_fnt_default(n, P, D, conv, D, D, true, 1, work, st))) return rc;
+  const TileOps& ops = tile_ops(n);
+  if (!p->split && ops.plan_spec) {
+    // fused: one CTA for the indicator spectrum, one CTA per digit convolution
+    KArgs a;
+    a.n = n;
+    a.k = k;
+    a.L = n;
+    a.pat = sl.pat;
+    a.twf = p->tn.twf;
+    a.twi = p->tn.twi;
+    a.scale = p->ninv;
+    ops.plan_spec(a, sl.pos_d, spec, st);
+    ops.plan_conv(a, spec, p->ghat, D, conv, st);
+  } else {
+    launch_lg_init(sl.pat, ind, n, st);
+    launch_lg_scatter(sl.pos_d, k, sl.pat, ind, st);
+    if ((rc = run_fnt_default(n, ind, 1, spec, 1, 1, false, 1, work, st))) return rc;
+    launch_lg_mul(spec, p->ghat, D, n, P, st);
+    if ((rc = run_fnt_default(n, P, D, conv, D, D, true, 1, work, st))) return rc;
+  }
   if (!p->blocked) {
     launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, nullptr, sl.ahat,
                     st);

@@ -41,6 +41,10 @@ struct TileOps {
   Launch decode = nullptr;      // fused decode, k <= n/2
   Launch decode_split = nullptr;  // fused decode, k > n/2
   Launch poly_level = nullptr;  // product-tree level (L = 2d)
+  // log-domain pattern build (n = L): spectrum of the indicator, digit convolutions
+  void (*plan_spec)(const KArgs&, const uint32_t* pos, uint32_t* spec, cudaStream_t) = nullptr;
+  void (*plan_conv)(const KArgs&, const uint32_t* spec, const uint32_t* ghat, int D,
+                    uint32_t* conv, cudaStream_t) = nullptr;
 };
 
 // Registry filled by the instantiation units.
