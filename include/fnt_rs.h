@@ -166,6 +166,30 @@ int fnt_rs_decode_host(fnt_rs_plan plan, const uint32_t* h_recv, const uint32_t*
                        uint32_t npos, uint16_t* h_out, size_t W, void* workspace, void* stream);
 
 /*
+ * Encode without any allocation, scratch included (the paper has no
+ * counterpart; this is a deployment convenience).  Codes with n > 8192 are
+ * encoded in two passes that exchange data through n * W words of scratch;
+ * fnt_rs_encode takes that scratch from the caller, this call takes it from a
+ * fixed device array of FNT_RS_NOALLOC_SCRATCH_BYTES that the library keeps on
+ * every GPU it is loaded on until the process exits.  It is meant for callers
+ * that cannot allocate device memory once they are running: services that
+ * pre-reserve all device memory at start-up (or run inside a framework whose
+ * allocator owns it) and so have no workspace to hand over, and latency-bound
+ * pipelines that must not hit cudaMalloc's implicit device synchronisation or
+ * an out-of-memory failure in the middle of a stream.
+ *   - Same arguments and result as fnt_rs_encode, minus the workspace.
+ *   - n * W * 4 > FNT_RS_NOALLOC_SCRATCH_BYTES: returns FNT_RS_E_WORKSPACE
+ *     without launching anything (split the batch into smaller W).
+ *   - n <= 8192 needs no scratch and simply runs fnt_rs_encode.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU race.
+ */
+#define FNT_RS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fnt_rs_encode_noalloc(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                          size_t ld_enc, size_t W, void* stream);
+
+/*
  * Reads the plan's device status word (synchronising `stream`), clears it and
  * returns FNT_RS_OK, FNT_RS_E_RANGE or FNT_RS_E_TIMEOUT (the most severe seen).
  */

@@ -131,6 +131,25 @@ def fnt_rs_decode_host(plan, h_recv: torch.Tensor, positions, h_out: torch.Tenso
                                      W, _ptr(workspace), _stream(stream)), "fnt_rs_decode_host")
 
 
+def fnt_rs_encode_noalloc(plan, src: torch.Tensor, enc: torch.Tensor, stream=None):
+    """fnt_rs_encode without a workspace: scratch comes from the library's fixed device array.
+
+    For callers that cannot allocate device memory while running (all memory
+    reserved up front, or no cudaMalloc allowed on the hot path).  Requests
+    with n * W * 4 bytes above FNT_RS_NOALLOC_SCRATCH_BYTES raise FntRsError
+    (code -9); concurrent calls on different streams share the scratch.
+    """
+    W, ld_src = _cols(src)
+    W2, ld_enc = _cols(enc)
+    if W2 != W:
+        raise ValueError("src and enc must have the same number of columns")
+    _check(load().fnt_rs_encode_noalloc(plan, _ptr(src), ld_src, _ptr(enc), ld_enc, W,
+                                        _stream(stream)), "fnt_rs_encode_noalloc")
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
 def fnt_rs_status(plan, stream=None) -> int:
     return int(load().fnt_rs_status(plan, _stream(stream)))
 

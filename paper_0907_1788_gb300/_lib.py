@@ -53,6 +53,7 @@ def load(build_if_missing: bool = False):
             "fnt_rs_decode_slots": (i32, [vp, vp, sz, vp, u32, vp, sz, sz, vp, vp]),
             "fnt_rs_fnt": (i32, [vp, vp, sz, vp, sz, sz, i32, vp, vp]),
             "fnt_rs_encode_host": (i32, [vp, vp, vp, sz, vp, vp]),
+            "fnt_rs_encode_noalloc": (i32, [vp, vp, sz, vp, sz, sz, vp]),
             "fnt_rs_decode_host": (i32, [vp, vp, vp, u32, vp, sz, vp, vp]),
             "fnt_rs_status": (i32, [vp, vp]),
             "fnt_rs_strerror": (ctypes.c_char_p, [i32]),

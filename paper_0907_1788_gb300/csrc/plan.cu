@@ -794,7 +794,9 @@ const char* fnt_rs_strerror(int code) {
     case FNT_RS_E_CUDA: return "CUDA runtime error";
     case FNT_RS_E_RANGE: return "value out of range (decoded 65536 or received > 65536)";
     case FNT_RS_E_TIMEOUT: return "a bounded device wait gave up";
-    case FNT_RS_E_WORKSPACE: return "workspace missing or too small";
+    case FNT_RS_E_WORKSPACE:
+      return "workspace missing or too small (or, for fnt_rs_encode_noalloc, n * W * 4 "
+             "exceeds FNT_RS_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown status";
   }
 }
