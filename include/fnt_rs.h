@@ -132,6 +132,20 @@ int fnt_rs_decode(fnt_rs_plan plan, const uint32_t* recv, size_t ld_recv,
                   size_t W, void* workspace, void* stream);
 
 /*
+ * Lossless decode (Sec. II.B: with nothing lost, decoding is the product by
+ * the inverse FNT matrix and the decoded symbols are its first k outputs):
+ * out[j][c] = (n^-1 sum_i enc[i][c] r^(-ij)) for j < k, one inverse FNT per
+ * codeword instead of the three transforms of the interpolation.  enc:
+ * device [n][ld_enc] uint32 holding all n symbols in position order; out:
+ * device [k][ld_out] uint16.  For a valid codeword this equals fnt_rs_decode
+ * with any k positions; for other inputs it is the first k coefficients of
+ * the degree < n interpolant.  A value 65536 is written as 0 and raises
+ * FNT_RS_E_RANGE in the status word.  workspace: FNT_RS_OP_FNT bytes.
+ */
+int fnt_rs_decode_full(fnt_rs_plan plan, const uint32_t* enc, size_t ld_enc, uint16_t* out,
+                       size_t ld_out, size_t W, void* workspace, void* stream);
+
+/*
  * Erasure decode from a receiver's slot buffer (Sec. II.B, same steps as
  * fnt_rs_decode): slots is a device [n][ld_slots] uint32 matrix whose row z
  * holds the symbols received at position z (rows of erased positions are
@@ -194,6 +208,45 @@ int fnt_rs_encode_noalloc(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, 
  * returns FNT_RS_OK, FNT_RS_E_RANGE or FNT_RS_E_TIMEOUT (the most severe seen).
  */
 int fnt_rs_status(fnt_rs_plan plan, void* stream);
+
+/*
+ * Ragged batches (many codeword groups of different n, k, W and erasure
+ * pattern in one launch).  Each group is one round trip of the method:
+ * encode src -> enc (Sec. II.B), build the group's pattern tables from the
+ * first k of `positions` (steps 1-3), decode every codeword from enc used as
+ * the receiver's slot buffer (row z = position z, steps 4-6) into out.
+ * Groups with positions == NULL are encode-only.  All pointers are device
+ * pointers except `positions` (host, copied at creation).  The library owns
+ * one plan per distinct (n, k), each decode group's pattern tables and the
+ * split-transform workspace; creation runs the batch once (uncaptured) and
+ * captures it into one CUDA graph over up to `nstreams` streams.
+ */
+typedef struct fnt_rs_group_s {
+  uint32_t n, k;
+  size_t W;
+  const uint16_t* src;
+  size_t ld_src;
+  uint32_t* enc;
+  size_t ld_enc;
+  const uint32_t* positions; /* host, npos >= k entries; NULL: encode only */
+  uint32_t npos;
+  uint16_t* out;
+  size_t ld_out;
+} fnt_rs_group;
+
+typedef struct fnt_rs_ragged_s* fnt_rs_ragged;
+
+int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_t ngroups,
+                         uint32_t nstreams, void* stream);
+/* Replays the captured graph on `stream` (one graph launch, no host sync). */
+int fnt_rs_ragged_run(fnt_rs_ragged r, void* stream);
+/* The same work as plain per-group calls on `stream`, one after another (baseline). */
+int fnt_rs_ragged_run_plain(fnt_rs_ragged r, void* stream);
+/* ORs the status words of the batch's plans (synchronises `stream`). */
+int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream);
+/* {groups, plans, streams}; returns the number of ints written. */
+int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap);
+void fnt_rs_ragged_destroy(fnt_rs_ragged r);
 
 /* Static description of a status code. */
 const char* fnt_rs_strerror(int code);

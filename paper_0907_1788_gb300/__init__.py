@@ -19,7 +19,7 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import FntRsError, LIB_PATH, load  # noqa: F401
+from ._lib import FntRsError, Group, LIB_PATH, load  # noqa: F401
 
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
@@ -107,6 +107,15 @@ def fnt_rs_decode_slots(plan, slots: torch.Tensor, positions, out: torch.Tensor,
            "fnt_rs_decode_slots")
 
 
+def fnt_rs_decode_full(plan, enc: torch.Tensor, out: torch.Tensor, workspace=None, stream=None):
+    W, ld = _cols(enc)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("enc and out must have the same number of columns")
+    _check(load().fnt_rs_decode_full(plan, _ptr(enc), ld, _ptr(out), ld_out, W, _ptr(workspace),
+                                     _stream(stream)), "fnt_rs_decode_full")
+
+
 def fnt_rs_fnt(plan, x: torch.Tensor, out: torch.Tensor, inverse: bool = False, workspace=None,
                stream=None):
     W, ld_in = _cols(x)
@@ -148,6 +157,52 @@ def fnt_rs_encode_noalloc(plan, src: torch.Tensor, enc: torch.Tensor, stream=Non
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def fnt_rs_ragged_create(groups, nstreams: int = 8, stream=None) -> int:
+    """groups: sequence of dicts with n, k, src, enc and optional positions, out (tensors)."""
+    arr = (Group * len(groups))()
+    keep = []
+    for i, g in enumerate(groups):
+        W, ld_src = _cols(g["src"])
+        _, ld_enc = _cols(g["enc"])
+        e = arr[i]
+        e.n, e.k, e.W = g["n"], g["k"], W
+        e.src, e.ld_src = _ptr(g["src"]), ld_src
+        e.enc, e.ld_enc = _ptr(g["enc"]), ld_enc
+        if g.get("positions") is not None:
+            pos = _positions(g["positions"])
+            keep.append(pos)
+            e.positions, e.npos = pos.ctypes.data, len(pos)
+            _, ld_out = _cols(g["out"])
+            e.out, e.ld_out = _ptr(g["out"]), ld_out
+    h = ctypes.c_void_p()
+    _check(load().fnt_rs_ragged_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p),
+                                       len(groups), nstreams, _stream(stream)),
+           "fnt_rs_ragged_create")
+    return h.value
+
+
+def fnt_rs_ragged_run(r, stream=None):
+    _check(load().fnt_rs_ragged_run(r, _stream(stream)), "fnt_rs_ragged_run")
+
+
+def fnt_rs_ragged_run_plain(r, stream=None):
+    _check(load().fnt_rs_ragged_run_plain(r, _stream(stream)), "fnt_rs_ragged_run_plain")
+
+
+def fnt_rs_ragged_status(r, stream=None) -> int:
+    return int(load().fnt_rs_ragged_status(r, _stream(stream)))
+
+
+def fnt_rs_ragged_info(r) -> dict:
+    buf = (ctypes.c_int * 3)()
+    m = load().fnt_rs_ragged_info(r, buf, 3)
+    return dict(zip(["groups", "plans", "streams"], [int(buf[i]) for i in range(m)]))
+
+
+def fnt_rs_ragged_destroy(r):
+    load().fnt_rs_ragged_destroy(r)
 
 
 def fnt_rs_status(plan, stream=None) -> int:
@@ -223,6 +278,13 @@ class Plan:
             out = torch.empty((self.k, W), dtype=torch.int16, device=slots.device)
         fnt_rs_decode_slots(self.handle, slots, positions, out, self.workspace(W, OP_DECODE),
                             stream)
+        return out
+
+    def decode_full(self, enc: torch.Tensor, out=None, stream=None):
+        W = enc.shape[1]
+        if out is None:
+            out = torch.empty((self.k, W), dtype=torch.int16, device=enc.device)
+        fnt_rs_decode_full(self.handle, enc, out, self.workspace(W, OP_FNT), stream)
         return out
 
     def fnt(self, x: torch.Tensor, inverse: bool = False, out=None, stream=None):

@@ -51,11 +51,18 @@ def load(build_if_missing: bool = False):
             "fnt_rs_decode_prepare": (i32, [vp, vp, u32, vp]),
             "fnt_rs_decode": (i32, [vp, vp, sz, vp, u32, vp, sz, sz, vp, vp]),
             "fnt_rs_decode_slots": (i32, [vp, vp, sz, vp, u32, vp, sz, sz, vp, vp]),
+            "fnt_rs_decode_full": (i32, [vp, vp, sz, vp, sz, sz, vp, vp]),
             "fnt_rs_fnt": (i32, [vp, vp, sz, vp, sz, sz, i32, vp, vp]),
             "fnt_rs_encode_host": (i32, [vp, vp, vp, sz, vp, vp]),
             "fnt_rs_encode_noalloc": (i32, [vp, vp, sz, vp, sz, sz, vp]),
             "fnt_rs_decode_host": (i32, [vp, vp, vp, u32, vp, sz, vp, vp]),
             "fnt_rs_status": (i32, [vp, vp]),
+            "fnt_rs_ragged_create": (i32, [ctypes.POINTER(vp), vp, u32, u32, vp]),
+            "fnt_rs_ragged_run": (i32, [vp, vp]),
+            "fnt_rs_ragged_run_plain": (i32, [vp, vp]),
+            "fnt_rs_ragged_status": (i32, [vp, vp]),
+            "fnt_rs_ragged_info": (i32, [vp, ctypes.POINTER(i32), i32]),
+            "fnt_rs_ragged_destroy": (None, [vp]),
             "fnt_rs_strerror": (ctypes.c_char_p, [i32]),
             "fnt_rs_launch_count": (ctypes.c_uint64, []),
             "fnt_rs_plan_info": (i32, [vp, ctypes.POINTER(i32), i32]),
@@ -66,6 +73,16 @@ def load(build_if_missing: bool = False):
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+class Group(ctypes.Structure):
+    """fnt_rs_group of include/fnt_rs.h."""
+
+    _fields_ = [("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("W", ctypes.c_size_t),
+                ("src", ctypes.c_void_p), ("ld_src", ctypes.c_size_t),
+                ("enc", ctypes.c_void_p), ("ld_enc", ctypes.c_size_t),
+                ("positions", ctypes.c_void_p), ("npos", ctypes.c_uint32),
+                ("out", ctypes.c_void_p), ("ld_out", ctypes.c_size_t)]
 
 
 def declared_symbols():

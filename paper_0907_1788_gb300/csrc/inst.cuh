@@ -112,6 +112,7 @@ TileOps make_tile_ops() {
   ops.encode = &launch_tile<S, W1, NT, false, LoadSrcFold<W1>, StoreRows32<W1>>;
   ops.fnt_fwd = &launch_tile<S, W1, NT, false, LoadRows32<W1>, StoreRows32<W1>>;
   ops.fnt_inv = &launch_tile<S, W1, NT, true, LoadRows32<W1>, StoreRows32<W1>>;
+  ops.lossless = &launch_tile<S, W1, NT, true, LoadRows32<W1>, StoreFirstK16<W1>>;
   ops.decode = &launch_decode<S, W1, NT>;
   ops.decode_split = &launch_decode_split<S, W2, NT>;
   if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;

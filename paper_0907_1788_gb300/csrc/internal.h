@@ -1,0 +1,91 @@
+// Internal declarations shared by the host modules of libfntrs (plans,
+// ragged batches, the serving loop).  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/fnt_rs.h"
+
+namespace fntrs {
+
+// Device tables per transform length L: per-pass schedule tables and the
+// powers r_L^e, r_L^-e (default root).
+struct Tables {
+  uint32_t* twf = nullptr;
+  uint32_t* twi = nullptr;
+  uint32_t* powf = nullptr;
+  uint32_t* powi = nullptr;
+};
+
+// Per-pattern device tables (steps 1-3 of the interpolation, Sec. II.B).
+struct PatternSlot {
+  std::vector<uint32_t> key;
+  uint64_t last_use = 0;
+  bool valid = false;
+  uint2* pat = nullptr;
+  uint32_t* ahat = nullptr;
+  uint32_t* ahat2 = nullptr;
+  uint32_t* pat32 = nullptr;  // (row << 17) | weight per position
+  uint32_t* pos_d = nullptr;  // first k positions (device)
+  uint32_t* pos_h = nullptr;  // pinned staging of the upload
+  cudaEvent_t staged = nullptr;  // recorded after the upload
+};
+
+constexpr int kPatternSlots = 4;
+constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
+
+}  // namespace fntrs
+
+struct fnt_rs_plan_s {
+  int dev = 0;
+  uint32_t n = 0, k = 0, root = 0;
+  uint32_t u = 1, uinv = 1;  // root = default^u; spectrum index j -> row uinv*j
+  uint32_t ninv = 1;
+  bool split = false;  // n > tile limit: n = C * kLocalL
+  int C = 1;
+  bool blocked = false;  // k > n/2
+  fntrs::Tables tn;             // tables of length n (pow tables; schedule tables if n <= tile)
+  fntrs::Tables tl;             // tables of the local length (split only)
+  fntrs::Tables tenc;           // schedule tables of the TMA encode's tile length
+  uint32_t* twc = nullptr;  // TMA encode, class 1 of n = 2L: pass-1 twiddles times r_n^i2
+  // log-domain pattern build: digits of g[d] = log_3(1 - r^d), b bits each
+  bool plan_tree = false;   // use the product tree instead
+  int lg_b = 4, lg_D = 4;
+  uint32_t* ghat = nullptr;  // [n][D] transforms of the reversed digit vectors
+  uint32_t* exp3 = nullptr;  // shared table
+  int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
+  bool no_tma = false;
+  int sms = 1;
+  int* status = nullptr;
+  uint32_t* pscratch = nullptr;
+  size_t pscratch_words = 0;
+  fntrs::PatternSlot slots[fntrs::kPatternSlots];
+  int current = -1;
+  uint64_t clock = 0;
+};
+
+namespace fntrs {
+
+int cuda_ok(cudaError_t e);
+size_t split_chunk(uint32_t n, int nbuf);
+int enc_nbuf(const fnt_rs_plan_s* p);
+int dec_nbuf(const fnt_rs_plan_s* p);
+int fnt_nbuf(const fnt_rs_plan_s* p);
+size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf);
+int get_tables(int L, Tables* out);
+uint32_t hinv(uint32_t a);
+int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos);
+// build the pattern of the positions already uploaded to sl.pos_d
+int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
+int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
+int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
+              size_t W, void* workspace, cudaStream_t st);
+// decode with explicit pattern tables (slots != 0: row z of recv is position z)
+int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
+                     size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
+                     cudaStream_t st, int slots);
+
+}  // namespace fntrs

@@ -154,8 +154,10 @@ struct StoreLocal {
     } else if constexpr (MODE == LM_WORK_AHAT) {
       static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(v, __ldg(a.ahat + row));
     } else if constexpr (MODE == LM_OUT16) {
-      if ((int)row < a.out_limit)
+      if ((int)row < a.out_limit) {
+        if (a.scale != 1u) v = m_mul(v, a.scale);
         static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
+      }
     } else if constexpr (MODE == LM_SPLIT) {
       if ((int)row < a.h)
         static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
@@ -406,6 +408,29 @@ struct StoreOut16 {
     const int col = col0 + c;
     if (col >= W || j >= k) return;
     out[(size_t)j * ld + col] = to_symbol(v, bad);
+  }
+  __device__ __forceinline__ void flush() const {
+    if (bad > 65535u) atomicOr(status, ST_RANGE);
+  }
+};
+
+// Lossless decode (nothing erased, Sec. II.B): out row j < k = n^-1-scaled
+// inverse transform value j as a 16-bit symbol.
+template <int WT>
+struct StoreFirstK16 {
+  uint16_t* out;
+  size_t ld;
+  int* status;
+  int col0, W, k;
+  uint32_t scale, bad;
+  static __device__ __forceinline__ StoreFirstK16 make(const KArgs& a) {
+    return StoreFirstK16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, (int)blockIdx.x * WT,
+                         a.W, a.k, a.scale, 0u};
+  }
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
+    const int col = col0 + c;
+    if (col >= W || j >= k) return;
+    out[(size_t)j * ld + col] = to_symbol(m_mul(v, scale), bad);
   }
   __device__ __forceinline__ void flush() const {
     if (bad > 65535u) atomicOr(status, ST_RANGE);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/fnt_rs.h"
+#include "internal.h"
 #include "kargs.h"
 #include "sched.h"
 
@@ -122,7 +123,7 @@ static uint32_t hpow(uint32_t a, uint64_t e) {
   }
   return (uint32_t)r;
 }
-static uint32_t hinv(uint32_t a) { return hpow(a, FNT_RS_P - 2); }
+uint32_t hinv(uint32_t a) { return hpow(a, FNT_RS_P - 2); }
 static int ilog2i(uint32_t v) {
   int b = 0;
   while ((1u << b) < v) ++b;
@@ -140,12 +141,6 @@ static uint32_t default_root(uint32_t n) { return hpow(3, 65536u / n); }
 // Device tables per transform length L (default root), shared by all plans
 // on a device: per-pass schedule tables and the powers r_L^e, r_L^-e.
 // ---------------------------------------------------------------------------
-struct Tables {
-  uint32_t* twf = nullptr;
-  uint32_t* twi = nullptr;
-  uint32_t* powf = nullptr;
-  uint32_t* powi = nullptr;
-};
 
 static std::mutex g_tab_mu;
 static std::map<std::pair<int, int>, Tables> g_tables;
@@ -181,7 +176,7 @@ static int upload(uint32_t** dst, const std::vector<uint32_t>& v) {
   return FNT_RS_OK;
 }
 
-static int get_tables(int L, Tables* out) {
+int get_tables(int L, Tables* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FNT_RS_E_CUDA;
   std::lock_guard<std::mutex> lk(g_tab_mu);
@@ -241,72 +236,31 @@ static int get_exp3(uint32_t** out) {
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
-struct PatternSlot {
-  std::vector<uint32_t> key;
-  uint64_t last_use = 0;
-  bool valid = false;
-  uint2* pat = nullptr;
-  uint32_t* ahat = nullptr;
-  uint32_t* ahat2 = nullptr;
-  uint32_t* pat32 = nullptr;  // (row << 17) | weight per position
-  uint32_t* pos_d = nullptr;  // first k positions (device)
-  uint32_t* pos_h = nullptr;  // pinned staging of the upload
-  cudaEvent_t staged = nullptr;  // recorded after the upload
-};
 
-constexpr int kPatternSlots = 4;
-constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
 
 }  // namespace fntrs
 
 using namespace fntrs;
 
-struct fnt_rs_plan_s {
-  int dev = 0;
-  uint32_t n = 0, k = 0, root = 0;
-  uint32_t u = 1, uinv = 1;  // root = default^u; spectrum index j -> row uinv*j
-  uint32_t ninv = 1;
-  bool split = false;  // n > tile limit: n = C * kLocalL
-  int C = 1;
-  bool blocked = false;  // k > n/2
-  Tables tn;             // tables of length n (pow tables; schedule tables if n <= tile)
-  Tables tl;             // tables of the local length (split only)
-  Tables tenc;           // schedule tables of the TMA encode's tile length
-  uint32_t* twc = nullptr;  // TMA encode, class 1 of n = 2L: pass-1 twiddles times r_n^i2
-  // log-domain pattern build: digits of g[d] = log_3(1 - r^d), b bits each
-  bool plan_tree = false;   // use the product tree instead
-  int lg_b = 4, lg_D = 4;
-  uint32_t* ghat = nullptr;  // [n][D] transforms of the reversed digit vectors
-  uint32_t* exp3 = nullptr;  // shared table
-  int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
-  bool no_tma = false;
-  int sms = 1;
-  int* status = nullptr;
-  uint32_t* pscratch = nullptr;
-  size_t pscratch_words = 0;
-  PatternSlot slots[kPatternSlots];
-  int current = -1;
-  uint64_t clock = 0;
-};
 
 namespace fntrs {
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? FNT_RS_OK : FNT_RS_E_CUDA; }
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? FNT_RS_OK : FNT_RS_E_CUDA; }
 
 // columns per chunk of a split transform with `nbuf` [n][Wc] workspace buffers
-static size_t split_chunk(uint32_t n, int nbuf) {
+size_t split_chunk(uint32_t n, int nbuf) {
   size_t wc = kChunkBudget / ((size_t)nbuf * n * 4);
   wc = std::max<size_t>(8, wc / 8 * 8);
   return wc;
 }
 
-static int enc_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
-static int dec_nbuf(const fnt_rs_plan_s* p) { return p->split ? (p->blocked ? 4 : 2) : 0; }
-static int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+int enc_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+int dec_nbuf(const fnt_rs_plan_s* p) { return p->split ? (p->blocked ? 4 : 2) : 0; }
+int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
 
-static size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf) {
+size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf) {
   if (nbuf == 0 || W == 0) return 0;
   const size_t wc = std::min(W, split_chunk(p->n, nbuf));
   return (size_t)nbuf * p->n * wc * 4;
@@ -385,7 +339,7 @@ static size_t pattern_scratch_words(uint32_t n, uint32_t k) {
 }
 
 // Log-domain build of the pattern tables (see pattern.cu).
-static int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
+int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   const int n = (int)p->n, k = (int)p->k, D = p->lg_D;
   uint32_t* ind = p->pscratch;
   uint32_t* spec = ind + n;
@@ -430,7 +384,7 @@ static int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st)
   return cuda_ok(cudaGetLastError());
 }
 
-static int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
+int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   const int n = (int)p->n, k = (int)p->k;
   uint32_t* base = p->pscratch;
   size_t K2 = 1;
@@ -491,7 +445,7 @@ static int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   return cuda_ok(cudaGetLastError());
 }
 
-static int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos) {
+int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos) {
   if (!pos) return FNT_RS_E_ARG;
   if (npos < p->k) return FNT_RS_E_POSITIONS;
   std::vector<uint8_t> seen(p->n, 0);
@@ -583,7 +537,7 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   return cuda_ok(cudaGetLastError());
 }
 
-static int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
   const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
   if (t != 1) return t;
@@ -639,8 +593,8 @@ static int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint3
 
 // Persistent TMA-staged decode (packed rows, n <= tile limit, k <= n/2);
 // returns 1 if not applicable.
-static int decode_tma(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, uint16_t* out,
-                      size_t ld_out, size_t W, cudaStream_t st) {
+static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
+                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
   if (p->no_tma || p->split || p->blocked || p->n < 64) return 1;
   if ((reinterpret_cast<uintptr_t>(recv) % 16) != 0 || (ld_recv * 4) % 16 != 0) return 1;
   auto fn = tmap_encode_fn();
@@ -659,7 +613,6 @@ static int decode_tma(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, ui
          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 1;
-  const PatternSlot& sl = p->slots[p->current];
   KArgs a;
   a.out = out;
   a.ld_out = ld_out;
@@ -682,13 +635,13 @@ static int decode_tma(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, ui
   return cuda_ok(cudaGetLastError());
 }
 
-static int do_decode(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv, uint16_t* out,
-                     size_t ld_out, size_t W, void* workspace, cudaStream_t st, int slots) {
+int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
+                     size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
+                     cudaStream_t st, int slots) {
   if (!slots) {
-    const int t = decode_tma(p, recv, ld_recv, out, ld_out, W, st);
+    const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st);
     if (t != 1) return t;
   }
-  const PatternSlot& sl = p->slots[p->current];
   KArgs a;
   a.slots = slots;
   a.in = recv;
@@ -994,7 +947,8 @@ int fnt_rs_decode(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv, const uin
   int rc = prepare(p, positions, npos, S(stream));
   if (rc) return rc;
   if (W == 0) return FNT_RS_OK;
-  return do_decode(p, recv, ld_recv, out, ld_out, W, workspace, S(stream), 0);
+  return do_decode_tables(p, p->slots[p->current], recv, ld_recv, out, ld_out, W, workspace,
+                          S(stream), 0);
 }
 
 int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
@@ -1008,7 +962,63 @@ int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
   int rc = prepare(p, positions, npos, S(stream));
   if (rc) return rc;
   if (W == 0) return FNT_RS_OK;
-  return do_decode(p, slots, ld_slots, out, ld_out, W, workspace, S(stream), 1);
+  return do_decode_tables(p, p->slots[p->current], slots, ld_slots, out, ld_out, W, workspace,
+                          S(stream), 1);
+}
+
+int fnt_rs_decode_full(fnt_rs_plan p, const uint32_t* enc, size_t ld_enc, uint16_t* out,
+                       size_t ld_out, size_t W, void* workspace, void* stream) {
+  if (!p) return FNT_RS_E_ARG;
+  if (W == 0) return FNT_RS_OK;
+  if (!enc || !out || ld_enc < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if (!aligned(enc, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
+  if (ws_bytes(p, W, fnt_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  cudaStream_t st = S(stream);
+  KArgs a;
+  a.in = enc;
+  a.ld_in = ld_enc;
+  a.out = out;
+  a.ld_out = ld_out;
+  a.n = (int)p->n;
+  a.k = (int)p->k;
+  a.scale = p->ninv;
+  a.in_row_mul = p->uinv;
+  a.status = p->status;
+  if (!p->split) {
+    a.W = (int)W;
+    a.L = (int)p->n;
+    a.C = 1;
+    a.twf = p->tn.twf;
+    a.twi = p->tn.twi;
+    tile_ops((int)p->n).lossless(a, 1, st);
+    return cuda_ok(cudaGetLastError());
+  }
+  const size_t wc = split_chunk(p->n, 1);
+  uint32_t* work = static_cast<uint32_t*>(workspace);
+  for (size_t c0 = 0; c0 < W; c0 += wc) {
+    const int w = (int)std::min(wc, W - c0);
+    KArgs c = a;
+    c.in = enc + c0;
+    c.out = out + c0;
+    c.W = w;
+    c.L = kLocalL;
+    c.C = p->C;
+    c.row_limit = (int)p->n;
+    c.out2 = work;
+    c.ld_work = (size_t)w;
+    c.powf = p->tn.powf;
+    c.powi = p->tn.powi;
+    cross_launcher(p->C, true, CL_U32)(c, 1, st);
+    KArgs b = c;
+    b.in = work;
+    b.ld_in = (size_t)w;
+    b.in_row_mul = 1;
+    b.out_limit = (int)p->k;
+    b.twf = p->tl.twf;
+    b.twi = p->tl.twi;
+    local_launcher(true, LM_OUT16)(b, p->C, st);
+  }
+  return cuda_ok(cudaGetLastError());
 }
 
 int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, size_t ld_out,

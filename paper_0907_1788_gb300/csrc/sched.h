@@ -38,6 +38,7 @@ struct TileOps {
   Launch encode = nullptr;      // fold-load source, rows cc + C*j
   Launch fnt_fwd = nullptr;     // rows -> rows, scaled
   Launch fnt_inv = nullptr;
+  Launch lossless = nullptr;    // inverse transform, first k rows as 16-bit symbols
   Launch decode = nullptr;      // fused decode, k <= n/2
   Launch decode_split = nullptr;  // fused decode, k > n/2
   Launch poly_level = nullptr;  // product-tree level (L = 2d)

@@ -279,6 +279,24 @@ def test_lossless_is_inverse_fnt(pkg):
     assert np.array_equal(back[:k], src.astype(np.uint32)) and not back[k:].any()
 
 
+@pytest.mark.parametrize("n,k,W", [(8, 5, 3), (512, 256, 40), (8192, 4096, 24), (16384, 9000, 8),
+                                   (65536, 32768, 4)])
+def test_lossless_fast_path(pkg, n, k, W):
+    # Sec. II.B: nothing lost -> first k outputs of the inverse FNT
+    src = synth.source(n + k + 3, k, W)
+    plan = pkg.Plan(n, k)
+    enc = plan.encode(pkg.to_device(src))
+    assert np.array_equal(pkg.to_host(plan.decode_full(enc)), src)
+    # arbitrary words: the first k coefficients of the degree < n interpolant
+    v = synth.received_uniform(n + 7, n, 2)
+    got = pkg.to_host(plan.decode_full(pkg.to_device(v)))
+    want = oracle.dft(v, inverse=True)[:k] if n <= 8192 else None
+    if want is not None:
+        flag = (want == 65536).any()
+        assert np.array_equal(got, np.where(want == 65536, 0, want).astype(np.uint16))
+        assert plan.status() == (pkg.E_RANGE if flag else 0)
+
+
 def test_host_buffer_entry_points(pkg):
     n, k, W = 2048, 1024, 48
     src = synth.source(88, k, W)
