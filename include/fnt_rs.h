@@ -248,6 +248,54 @@ int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream);
 int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap);
 void fnt_rs_ragged_destroy(fnt_rs_ragged r);
 
+/*
+ * Serving loop (continuous batching).  A dispatcher thread admits requests
+ * in arrival order as stream slots and device memory free up: each request's
+ * input and output live in an arena of `budget_bytes` reserved at creation
+ * (the admission budget); requests that arrive while others run start on
+ * their own streams and overlap with them.  Plans, twiddle tables and the
+ * per-pattern locator tables (steps 1-3, Sec. II.B; an LRU pool per plan)
+ * stay resident.  A request's input is generated on the device from `seed`:
+ * uniform 16-bit source symbols (encode, [k][W]) or uniform values in
+ * [0, 65536] received at `positions` (decode, [k][W]).
+ */
+typedef struct fnt_rs_request_s {
+  int op; /* FNT_RS_OP_ENCODE or FNT_RS_OP_DECODE */
+  uint32_t n, k, W;
+  uint64_t seed;
+  const uint32_t* positions; /* decode: host, >= k entries, copied at submit */
+  uint32_t npos;
+} fnt_rs_request;
+
+typedef struct fnt_rs_server_s* fnt_rs_server;
+
+/* keep_results = 0 frees a request's buffers as soon as it completes. */
+int fnt_rs_server_create(fnt_rs_server* out, size_t budget_bytes, uint32_t nstreams,
+                         int keep_results);
+/* Creates the plan of (n, k) now instead of at its first request. */
+int fnt_rs_server_preplan(fnt_rs_server s, uint32_t n, uint32_t k);
+/* Queues a request; FNT_RS_E_BUDGET if its buffers alone exceed the budget. */
+int fnt_rs_server_submit(fnt_rs_server s, const fnt_rs_request* req, uint64_t* ticket);
+/* 1 done (latency in *latency_ms), 0 queued or running, negative: its error. */
+int fnt_rs_server_poll(fnt_rs_server s, uint64_t ticket, double* latency_ms);
+/* Blocks until every submitted request has finished. */
+int fnt_rs_server_drain(fnt_rs_server s);
+/* Copies a finished request's input / output (kept results) to host memory. */
+int fnt_rs_server_fetch(fnt_rs_server s, uint64_t ticket, void* h_in, void* h_out);
+/* Frees a finished request's buffers and record. */
+int fnt_rs_server_release(fnt_rs_server s, uint64_t ticket);
+/* {completed, rejected, arena bytes in use, arena bytes, resident plans}. */
+int fnt_rs_server_stats(fnt_rs_server s, double* out, int cap);
+void fnt_rs_server_destroy(fnt_rs_server s);
+/* Submits reqs[i] at arrival_s[i] seconds (real time) and records latency_ms[i]
+ * (-1: refused); *wall_s = duration of the replay. */
+int fnt_rs_server_replay(fnt_rs_server s, const fnt_rs_request* reqs, const double* arrival_s,
+                         uint32_t count, double* latency_ms, double* wall_s);
+/* Same trace through the plain path: one request at a time, its plan and
+ * pattern built per request, on `stream`. */
+int fnt_rs_baseline_replay(const fnt_rs_request* reqs, const double* arrival_s, uint32_t count,
+                           double* latency_ms, double* wall_s, void* stream);
+
 /* Static description of a status code. */
 const char* fnt_rs_strerror(int code);
 

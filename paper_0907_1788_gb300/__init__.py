@@ -19,7 +19,7 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import FntRsError, Group, LIB_PATH, load  # noqa: F401
+from ._lib import FntRsError, Group, LIB_PATH, Request, load  # noqa: F401
 
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
@@ -203,6 +203,102 @@ def fnt_rs_ragged_info(r) -> dict:
 
 def fnt_rs_ragged_destroy(r):
     load().fnt_rs_ragged_destroy(r)
+
+
+def _requests(reqs):
+    """Marshal request dicts (op, n, k, W, seed, positions) into a ctypes array."""
+    arr = (Request * len(reqs))()
+    keep = []
+    for i, q in enumerate(reqs):
+        e = arr[i]
+        e.op = OP_DECODE if q["op"] == "decode" else OP_ENCODE
+        e.n, e.k, e.W, e.seed = q["n"], q["k"], q["W"], q["seed"]
+        if q.get("positions") is not None:
+            pos = _positions(q["positions"])
+            keep.append(pos)
+            e.positions, e.npos = pos.ctypes.data, len(pos)
+    return arr, keep
+
+
+def fnt_rs_server_create(budget_bytes: int, nstreams: int = 8, keep_results: bool = True) -> int:
+    h = ctypes.c_void_p()
+    _check(load().fnt_rs_server_create(ctypes.byref(h), budget_bytes, nstreams,
+                                       int(keep_results)), "fnt_rs_server_create")
+    return h.value
+
+
+def fnt_rs_server_preplan(server, n: int, k: int):
+    _check(load().fnt_rs_server_preplan(server, n, k), "fnt_rs_server_preplan")
+
+
+def fnt_rs_server_submit(server, req: dict) -> int:
+    arr, keep = _requests([req])
+    t = ctypes.c_uint64()
+    _check(load().fnt_rs_server_submit(server, ctypes.cast(arr, ctypes.c_void_p),
+                                       ctypes.byref(t)), "fnt_rs_server_submit")
+    return t.value
+
+
+def fnt_rs_server_poll(server, ticket: int):
+    lat = ctypes.c_double(0)
+    rc = load().fnt_rs_server_poll(server, ticket, ctypes.byref(lat))
+    if rc < 0:
+        raise FntRsError(rc, "fnt_rs_server_poll")
+    return (rc == 1), lat.value
+
+
+def fnt_rs_server_drain(server):
+    _check(load().fnt_rs_server_drain(server), "fnt_rs_server_drain")
+
+
+def fnt_rs_server_fetch(server, ticket: int, req: dict):
+    """Return (input, output) host arrays of a finished request."""
+    n, k, W = req["n"], req["k"], req["W"]
+    if req["op"] == "encode":
+        h_in, h_out = np.empty((k, W), np.uint16), np.empty((n, W), np.uint32)
+    else:
+        h_in, h_out = np.empty((k, W), np.uint32), np.empty((k, W), np.uint16)
+    _check(load().fnt_rs_server_fetch(server, ticket, h_in.ctypes.data, h_out.ctypes.data),
+           "fnt_rs_server_fetch")
+    return h_in, h_out
+
+
+def fnt_rs_server_release(server, ticket: int):
+    _check(load().fnt_rs_server_release(server, ticket), "fnt_rs_server_release")
+
+
+def fnt_rs_server_stats(server) -> dict:
+    buf = (ctypes.c_double * 5)()
+    m = load().fnt_rs_server_stats(server, buf, 5)
+    keys = ["completed", "rejected", "arena_used", "arena_bytes", "plans"]
+    return {keys[i]: buf[i] for i in range(m)}
+
+
+def fnt_rs_server_destroy(server):
+    load().fnt_rs_server_destroy(server)
+
+
+def fnt_rs_server_replay(server, reqs, arrivals):
+    """Replay a timed trace; returns (latency_ms array, wall seconds)."""
+    arr, keep = _requests(reqs)
+    t = np.ascontiguousarray(arrivals, dtype=np.float64)
+    lat = np.zeros(len(reqs), dtype=np.float64)
+    wall = ctypes.c_double(0)
+    _check(load().fnt_rs_server_replay(server, ctypes.cast(arr, ctypes.c_void_p), t.ctypes.data,
+                                       len(reqs), lat.ctypes.data, ctypes.byref(wall)),
+           "fnt_rs_server_replay")
+    return lat, wall.value
+
+
+def fnt_rs_baseline_replay(reqs, arrivals, stream=None):
+    arr, keep = _requests(reqs)
+    t = np.ascontiguousarray(arrivals, dtype=np.float64)
+    lat = np.zeros(len(reqs), dtype=np.float64)
+    wall = ctypes.c_double(0)
+    _check(load().fnt_rs_baseline_replay(ctypes.cast(arr, ctypes.c_void_p), t.ctypes.data,
+                                         len(reqs), lat.ctypes.data, ctypes.byref(wall),
+                                         _stream(stream)), "fnt_rs_baseline_replay")
+    return lat, wall.value
 
 
 def fnt_rs_status(plan, stream=None) -> int:

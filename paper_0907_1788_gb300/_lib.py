@@ -57,6 +57,17 @@ def load(build_if_missing: bool = False):
             "fnt_rs_encode_noalloc": (i32, [vp, vp, sz, vp, sz, sz, vp]),
             "fnt_rs_decode_host": (i32, [vp, vp, vp, u32, vp, sz, vp, vp]),
             "fnt_rs_status": (i32, [vp, vp]),
+            "fnt_rs_server_create": (i32, [ctypes.POINTER(vp), sz, u32, i32]),
+            "fnt_rs_server_preplan": (i32, [vp, u32, u32]),
+            "fnt_rs_server_submit": (i32, [vp, vp, ctypes.POINTER(ctypes.c_uint64)]),
+            "fnt_rs_server_poll": (i32, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+            "fnt_rs_server_drain": (i32, [vp]),
+            "fnt_rs_server_fetch": (i32, [vp, ctypes.c_uint64, vp, vp]),
+            "fnt_rs_server_release": (i32, [vp, ctypes.c_uint64]),
+            "fnt_rs_server_stats": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
+            "fnt_rs_server_destroy": (None, [vp]),
+            "fnt_rs_server_replay": (i32, [vp, vp, vp, u32, vp, vp]),
+            "fnt_rs_baseline_replay": (i32, [vp, vp, u32, vp, vp, vp]),
             "fnt_rs_ragged_create": (i32, [ctypes.POINTER(vp), vp, u32, u32, vp]),
             "fnt_rs_ragged_run": (i32, [vp, vp]),
             "fnt_rs_ragged_run_plain": (i32, [vp, vp]),
@@ -83,6 +94,14 @@ class Group(ctypes.Structure):
                 ("enc", ctypes.c_void_p), ("ld_enc", ctypes.c_size_t),
                 ("positions", ctypes.c_void_p), ("npos", ctypes.c_uint32),
                 ("out", ctypes.c_void_p), ("ld_out", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    """fnt_rs_request of include/fnt_rs.h."""
+
+    _fields_ = [("op", ctypes.c_int), ("n", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("W", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("positions", ctypes.c_void_p), ("npos", ctypes.c_uint32)]
 
 
 def declared_symbols():

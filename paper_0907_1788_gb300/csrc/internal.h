@@ -79,7 +79,9 @@ int get_tables(int L, Tables* out);
 uint32_t hinv(uint32_t a);
 int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos);
 // build the pattern of the positions already uploaded to sl.pos_d
-int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
+int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st,
+                      uint32_t* scratch = nullptr);
+size_t pattern_scratch_words(uint32_t n, uint32_t k);
 int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
               size_t W, void* workspace, cudaStream_t st);

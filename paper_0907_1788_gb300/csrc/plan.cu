@@ -326,7 +326,7 @@ static int run_fnt_default(int L, const uint32_t* in, size_t ld_in, uint32_t* ou
 // ---------------------------------------------------------------------------
 // pattern build (steps 1-3) into slot `si`
 // ---------------------------------------------------------------------------
-static size_t pattern_scratch_words(uint32_t n, uint32_t k) {
+size_t pattern_scratch_words(uint32_t n, uint32_t k) {
   // product tree: level ping-pong, [n][3] matrix + transform, big-level matrices + work
   size_t K2 = 1;
   while (K2 < k) K2 <<= 1;
@@ -338,10 +338,11 @@ static size_t pattern_scratch_words(uint32_t n, uint32_t k) {
   return std::max(tree, lg);
 }
 
-// Log-domain build of the pattern tables (see pattern.cu).
-int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
+// Log-domain build of the pattern tables (see pattern.cu); `scratch` holds
+// pattern_scratch_words(n, k) words (the plan's own scratch when null).
+int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32_t* scratch) {
   const int n = (int)p->n, k = (int)p->k, D = p->lg_D;
-  uint32_t* ind = p->pscratch;
+  uint32_t* ind = scratch ? scratch : p->pscratch;
   uint32_t* spec = ind + n;
   uint32_t* aval = spec + n;
   uint32_t* coef = aval + n;
