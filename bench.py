@@ -45,6 +45,61 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+ISSUE_PEAK_TOPS = 152 * 4 * 32 * 2.07e9 / 1e12  # int32 lane-instructions / s (issue bound)
+
+
+def fnt_instr(n: int) -> float:
+    """Instructions of one length-n FNT in the minimal Z/(2^32-1) formulation.
+
+    Radix-2 butterflies (n/2 log2 n) at 4 (add and sub, each with its carry
+    fold), the power-of-two rotations of the radix <= 32 passes at 1, the
+    general twiddles between passes at 3 (64-bit product + fold).
+    """
+    import math
+
+    lg = int(math.log2(n))
+    bfly = n // 2 * lg
+    radices = {4096: [16, 16, 16], 8192: [32, 16, 16]}.get(n, [n])
+    rot_per = {16: 17, 32: 49, 8: 5, 4: 1, 2: 0}
+    rot = sum(n // r * rot_per.get(r, 0) for r in radices)
+    tw = n * (len(radices) - 1)
+    return 4 * bfly + rot + 3 * tw
+
+
+def decode_instr(n: int, k: int) -> float:
+    """Per codeword: three FNT_n + weights (k), A^ product (n), output reduction (k)."""
+    return 3 * fnt_instr(n) + 3 * k + 3 * n + 4 * k
+
+
+def encode_instr(n: int, k: int) -> float:
+    """Per codeword: two FNT_(n/2) (k = n/2 classes) + class-1 twiddles + output reduction."""
+    return 2 * fnt_instr(n // 2) + 3 * (n // 2) + 4 * n
+
+
+def _src_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0907_1788_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the sources still match."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("src_hash") == _src_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
 class Clocks:
     """Samples nvidia-smi during the timed region."""
 
@@ -145,6 +200,96 @@ def cpu_baseline(seconds_target: float = 10.0):
             "sample": (f"{cols} codewords of {cfg.name} encoded (Horner) and decoded (Lagrange) on "
                        f"{threads} threads + one pattern build; scaled to the {cfg.W}-codeword "
                        f"batch: {per_batch:.2f} s per batch")}
+
+
+def ragged_measure(pkg, dev, budget_bytes=6 << 30, nstreams=16):
+    """One wave of the 4096-group ragged batch: graph launch vs per-group plain calls."""
+    import torch
+
+    specs = synth.ragged_groups(seed=4, groups=4096)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    groups, total, src_bytes = [], 0, 0
+    for g in specs:
+        n, k, W = g["n"], g["k"], g["W"]
+        size = k * W * 2 + n * W * 4 + k * W * 2
+        if total + size > budget_bytes:
+            continue
+        total += size
+        src_bytes += k * W * 2
+        src = torch.randint(0, 65536, (k, W), generator=gen, device=dev, dtype=torch.int32)
+        groups.append({"n": n, "k": k, "src": src.to(torch.int16),
+                       "enc": torch.empty((n, W), dtype=torch.int32, device=dev),
+                       "out": torch.empty((k, W), dtype=torch.int16, device=dev),
+                       "positions": g["positions"]})
+    r = pkg.fnt_rs_ragged_create(groups, nstreams=nstreams)
+    try:
+        st = torch.cuda.current_stream()
+
+        def timed(fn, reps):
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                fn(r, st)
+                b.record(st)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return min(ts)
+
+        g_ms = timed(pkg.fnt_rs_ragged_run, 3)
+        p_ms = timed(pkg.fnt_rs_ragged_run_plain, 2)
+        ok = all(torch.equal(g["out"], g["src"]) for g in groups[:: max(1, len(groups) // 16)])
+        ok = ok and pkg.fnt_rs_ragged_status(r) == 0
+        info = pkg.fnt_rs_ragged_info(r)
+    finally:
+        pkg.fnt_rs_ragged_destroy(r)
+    return {"groups": len(groups), "plans": info.get("plans"), "streams": info.get("streams"),
+            "wave_gb": total / 1e9, "source_gb": src_bytes / 1e9,
+            "graph_ms": g_ms, "plain_ms": p_ms,
+            "graph_gbs": src_bytes / (g_ms * 1e-3) / 1e9,
+            "plain_gbs": src_bytes / (p_ms * 1e-3) / 1e9,
+            "round_trip_ok": bool(ok),
+            "config": ("seed-4 ragged batch (n = 2^U{8..16}, k = floor(n*rho), rho in "
+                       "{1/2,2/3,3/4,7/8}, W = 2^U{8..12}/2, own uniform pattern): the groups "
+                       "that fit one 6 GB wave; each group = encode + pattern build + decode")}
+
+
+def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30):
+    """cfg5 trace head: continuous batching server vs one request at a time."""
+    reqs = synth.serving_requests(seed=5, rate_per_s=rate, duration_s=count / rate * 2)[:count]
+    trace = []
+    for q in reqs:
+        d = dict(op=q["op"], n=q["n"], k=q["k"], W=q["W"], seed=q["seed"])
+        if q["op"] == "decode":
+            d["positions"] = synth.received_positions(
+                q["n"], synth.erased_uniform(q["pattern_seed"], q["n"], q["k"]))
+        trace.append(d)
+    arrivals = [q["t"] for q in reqs]
+    src = sum(q["k"] * q["W"] * 2 for q in trace)
+    srv = pkg.fnt_rs_server_create(budget, nstreams=16, keep_results=False)
+    try:
+        for n in sorted({q["n"] for q in trace}):
+            for k in sorted({q["k"] for q in trace if q["n"] == n}):
+                pkg.fnt_rs_server_preplan(srv, n, k)
+        lat, wall = pkg.fnt_rs_server_replay(srv, trace, arrivals)
+        stats = pkg.fnt_rs_server_stats(srv)
+    finally:
+        pkg.fnt_rs_server_destroy(srv)
+    blat, bwall = pkg.fnt_rs_baseline_replay(trace, arrivals)
+    ok = lat[lat >= 0]
+    return {"rate_per_s": rate, "requests": len(trace), "completed": int(stats["completed"]),
+            "rejected": int((lat < 0).sum()),
+            "p50_ms": float(np.percentile(ok, 50)), "p99_ms": float(np.percentile(ok, 99)),
+            "achieved_gbs": src / wall / 1e9, "wall_s": wall,
+            "baseline": {"p50_ms": float(np.percentile(blat, 50)),
+                         "p99_ms": float(np.percentile(blat, 99)),
+                         "achieved_gbs": src / bwall / 1e9, "wall_s": bwall,
+                         "kind": "one request at a time, plan + pattern built per request"},
+            "budget_gb": budget / 2**30, "streams": 16,
+            "config": ("seed-5 Poisson trace (n = 2^U{9..16}, rho in {1/2,3/4}, packets "
+                       "2^U{10..14} B, half decode with 64 recurring patterns per shape), first "
+                       f"{len(trace)} requests; inputs generated on the device")}
 
 
 def run_reference(args):
@@ -266,15 +411,19 @@ def run_gpu(args):
     enc_ms, pat_ms, dec_ms = (statistics.mean(t_enc), statistics.mean(t_pat),
                               statistics.mean(t_dec))
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / duration)
+    # roofline of the dominant kernel: both are integer-issue bound, so the
+    # roof is the int32 issue rate; the HBM fraction is reported beside it
     hbm_peak, peak_src = _peaks()
     enc_bytes = W * (2 * k + 4 * n)
     dec_bytes = W * (4 * k + 2 * k) + n * 8 + n * 4
     if dec_ms >= enc_ms:
-        dom, dom_ms, dom_bytes = "decode", dec_ms, dec_bytes
+        dom, dom_ms, dom_bytes, dom_instr = "decode", dec_ms, dec_bytes, W * decode_instr(n, k)
+        dom_kernel = "k_decode_tma"
     else:
-        dom, dom_ms, dom_bytes = "encode", enc_ms, enc_bytes
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        dom, dom_ms, dom_bytes, dom_instr = "encode", enc_ms, enc_bytes, W * encode_instr(n, k)
+        dom_kernel = "k_encode_tma"
+    achieved_tops = dom_instr / (dom_ms * 1e-3) / 1e12
+    achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9
 
     # end to end through the host-buffer entry points (pinned memory)
     h_src = torch.from_numpy(cfg.source().view(np.int16)).pin_memory()
@@ -314,14 +463,22 @@ def run_gpu(args):
         "encode_gbs": src_bytes / (enc_ms * 1e-3) / 1e9,
         "decode_gbs": src_bytes / (dec_ms * 1e-3) / 1e9,
         "decode_incl_plan_gbs": src_bytes / ((dec_ms + pat_ms) * 1e-3) / 1e9,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                     "peak_source": peak_src},
+        "roofline": {"bound": "alu", "kernel": dom_kernel, "achieved": achieved_tops,
+                     "peak": ISSUE_PEAK_TOPS, "unit": "Tops/s", "frac": achieved_tops / ISSUE_PEAK_TOPS,
+                     "traffic": _traffic(dom_kernel),
+                     "ops_per_launch": dom_instr,
+                     "peak_source": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (int32 issue)",
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm_peak, "peak_source": peak_src,
+                             "bytes_per_launch": dom_bytes}},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "wall_ms_per_step": t_wall * 1e3 / args.steps,
         "clocks": clk.summary(),
     }
+    if world == 1 and not args.no_extras:
+        line["ragged"] = ragged_measure(pkg, dev)
+        line["serving"] = serving_measure(pkg)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -336,6 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ragged and serving runs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
