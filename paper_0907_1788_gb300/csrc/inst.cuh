@@ -80,23 +80,12 @@ void launch_poly_level(const KArgs& a, int, cudaStream_t st) {
 }
 
 template <class S, int NT>
-void launch_plan_spec(const KArgs& a, const uint32_t* pos, uint32_t* spec, cudaStream_t st) {
-  auto kern = k_plan_spec<S, NT>;
+void launch_plan_fused(const PlanArgs& pa, cudaStream_t st) {
+  auto kern = k_plan_fused<S, NT>;
   const int smem = (Lay<S, 1>::WORDS + S::L) * 4;
   struct Tag {};
   ensure_smem<Tag>(kern, smem);
-  kern<<<1, NT, smem, st>>>(a, pos, spec);
-  count_launch();
-}
-
-template <class S, int NT>
-void launch_plan_conv(const KArgs& a, const uint32_t* spec, const uint32_t* ghat, int D,
-                      uint32_t* conv, cudaStream_t st) {
-  auto kern = k_plan_conv<S, NT>;
-  const int smem = smem_words<S, 1>() * 4;
-  struct Tag {};
-  ensure_smem<Tag>(kern, smem);
-  kern<<<D, NT, smem, st>>>(a, spec, ghat, D, conv);
+  kern<<<pa.D, NT, smem, st>>>(pa);
   count_launch();
 }
 
@@ -117,18 +106,17 @@ TileOps make_tile_ops() {
   ops.decode_split = &launch_decode_split<S, W2, NT>;
   if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;
   if constexpr (L >= 64) {
-    ops.plan_spec = &launch_plan_spec<S, 512>;
-    ops.plan_conv = &launch_plan_conv<S, 512>;
+    ops.plan_fused = &launch_plan_fused<S, 512>;
   }
   return ops;
 }
 
 void register_ops(const TileOps& ops);
 
-// Persistent TMA-staged encode (k_encode_tma): dynamic shared memory bytes.
+// TMA-staged encode (k_encode_tma): dynamic shared memory bytes.
 template <class S, int WT>
 constexpr int encode_tma_smem(int rows_staged) {
-  return ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128 + rows_staged * WT * 2 + 16;
+  return ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128 + rows_staged * WT * 2 + kSchedBytes;
 }
 
 template <class S, int WT, int NT, int C>
@@ -159,13 +147,13 @@ template <class S, int WT, int NT>
 int launch_decode_tma_t(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
   auto kern = k_decode_tma<S, WT, NT>;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
-  const int smem = work + t.rows_staged * WT * 4 + 16;
+  const int smem = work + t.rows_staged * WT * 4 + kSchedBytes;
   static bool done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!done[dev & 63]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             work + decode_tma_max_rows(S::L) * WT * 4 + 16) != cudaSuccess)
+                             work + decode_tma_max_rows(S::L) * WT * 4 + kSchedBytes) != cudaSuccess)
       return -1;
     done[dev & 63] = true;
   }

@@ -31,8 +31,15 @@ struct PatternSlot {
   uint32_t* pat32 = nullptr;  // (row << 17) | weight per position
   uint32_t* pos_d = nullptr;  // first k positions (device)
   uint32_t* pos_h = nullptr;  // pinned staging of the upload
-  cudaEvent_t staged = nullptr;  // recorded after the upload
+  const uint32_t* pos_map = nullptr;  // pos_h as seen from the device (mapped pinned memory)
+  cudaEvent_t staged = nullptr;  // recorded once the device has read pos_h
+  uint32_t* done = nullptr;   // completion counter of the one-launch build (zero at rest)
 };
+
+// Device tables of one erasure pattern for length n (and, with `staging`, the
+// pinned upload buffer and its event); release with free_pattern_tables.
+int alloc_pattern_tables(PatternSlot& sl, size_t n, bool staging);
+void free_pattern_tables(PatternSlot& sl);
 
 constexpr int kPatternSlots = 4;
 constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
@@ -78,9 +85,12 @@ size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf);
 int get_tables(int L, Tables* out);
 uint32_t hinv(uint32_t a);
 int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos);
-// build the pattern of the positions already uploaded to sl.pos_d
+// build the pattern of the positions already uploaded to sl.pos_d (or, for
+// the one-launch build, of the device-readable positions `pos`)
 int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st,
-                      uint32_t* scratch = nullptr);
+                      uint32_t* scratch = nullptr, const uint32_t* pos = nullptr);
+// the log-domain build of this plan runs as one launch (k_plan_fused)
+bool fused_plan_applies(const fnt_rs_plan_s* p);
 size_t pattern_scratch_words(uint32_t n, uint32_t k);
 int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,

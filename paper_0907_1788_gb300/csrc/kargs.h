@@ -62,4 +62,21 @@ struct KArgs {
   int nodes = 0;      // product-tree level: number of child nodes
 };
 
+// Arguments of the one-launch log-domain pattern build (n <= tile limit).
+struct PlanArgs {
+  int k = 0, D = 0, b = 0;
+  uint32_t ninv = 0;
+  const uint32_t* twf = nullptr;   // pass tables of the n-schedule, forward root
+  const uint32_t* twi = nullptr;   // same, inverse root
+  const uint32_t* pos = nullptr;   // first k received positions
+  const uint32_t* ghat = nullptr;  // [n][D] transforms of the log-table digits
+  const uint32_t* exp3 = nullptr;  // 3^e, e < 65536
+  uint32_t* conv = nullptr;        // [n][D] digit convolutions (scratch)
+  uint2* pat = nullptr;            // position table (written)
+  uint32_t* pat32 = nullptr;
+  uint32_t* aval = nullptr;        // A(r^j) (split step-6 product) or null
+  uint32_t* ahat = nullptr;        // n^-1 FNT(A mod x^k) or null
+  uint32_t* done = nullptr;        // CTA completion counter, zero between builds
+};
+
 }  // namespace fntrs

@@ -2,6 +2,7 @@
 // fused single-CTA decode, and one level of the locator product tree.
 #pragma once
 #include "kargs.h"
+#include "logplan.cuh"
 #include "tile.cuh"
 #include "tma.cuh"
 
@@ -214,14 +215,16 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent encode with TMA-staged source (n = C * L, C in {1, 2}, k <= L).
-// Each CTA walks column tiles of WT codewords; the [k][WT] source tile is
-// brought into shared memory by cp.async.bulk.tensor while the previous tile
-// is still being transformed.  For C = 2 the tile feeds both output classes:
+// Encode with TMA-staged source (n = C * L, C in {1, 2}, k <= L).  One CTA
+// per column tile of WT codewords; a running CTA takes over tiles of CTAs not
+// yet launched (cluster launch control, see clc_take), and the [k][WT] source
+// tile it takes over is brought into shared memory by cp.async.bulk.tensor
+// while the current tile is still being transformed.  For C = 2 the tile feeds both output classes:
 // class 1 takes x[i] = s_i r_n^i; with i = q*S1 + i2 the factor r_n^(q*S1) is
 // a power of two (r_n^S1 has order 2*R1 <= 32) and r_n^i2 rides on the pass-1
 // twiddle table twc (all R1 entries).
-// smem: work (Lay WORDS u32) | stage (rows_staged * WT u16) | mbarrier.
+// smem: work (Lay WORDS u32) | stage (rows_staged * WT u16) | barriers and
+// cancel response (kSchedBytes).
 // ---------------------------------------------------------------------------
 template <class S, int WT, int NT, int C>
 __global__ void __launch_bounds__(NT, 1)
@@ -237,26 +240,35 @@ __global__ void __launch_bounds__(NT, 1)
   uint16_t* stage = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(stage) +
                                               (size_t)rows_staged * WT * 2);
+  uint64_t* cbar = bar + 1;
+  uint4* resp = reinterpret_cast<uint4*>(bar + 2);
+  __shared__ int s_next;
   const int ntiles = (a.W + WT - 1) / WT;
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 2;
-  if (threadIdx.x == 0) mbar_init(bar, 1);
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init(cbar, 1);
+  }
   __syncthreads();
-  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+  if (threadIdx.x == 0 && tile < ntiles) {
     mbar_expect_tx(bar, tx_bytes);
     for (int bx = 0; bx < nbox; ++bx)
-      tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, (int)blockIdx.x * WT, bx * box_rows,
-                  bar);
+      tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, tile * WT, bx * box_rows, bar);
+    clc_request(resp, cbar);
   }
-  uint32_t parity = 0;
+  uint32_t parity = 0, cphase = 0;
+  bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
   uint32_t* out = static_cast<uint32_t*>(a.out);
   const size_t ld = a.ld_out;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  while (tile < ntiles) {
     const bool ok = mbar_wait(bar, parity);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(a.status, ST_TIMEOUT);
         mbar_wait(bar, parity);  // let the copy in flight land before exiting
+        if (pending) mbar_wait(cbar, cphase);
       }
       return;
     }
@@ -297,13 +309,22 @@ __global__ void __launch_bounds__(NT, 1)
         for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
       }
       __syncthreads();
-      if (cc == C - 1 && threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
-        // the stage is free: prefetch the next tile
-        fence_proxy_async();
-        mbar_expect_tx(bar, tx_bytes);
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, (tile + (int)gridDim.x) * WT,
-                      bx * box_rows, bar);
+      if (cc == C - 1 && threadIdx.x == 0) {
+        // the stage is free: take over a pending CTA's tile and prefetch it
+        int nxt = clc_take(resp, cbar, cphase);
+        pending = false;
+        if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+        if (nxt >= 0 && nxt < ntiles) {
+          fence_proxy_async();
+          mbar_expect_tx(bar, tx_bytes);
+          for (int bx = 0; bx < nbox; ++bx)
+            tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, nxt * WT, bx * box_rows, bar);
+          clc_request(resp, cbar);
+          pending = true;
+        } else {
+          nxt = ntiles;
+        }
+        s_next = nxt;
       }
       if constexpr (S::NP == 3) {
         dif_mid<S, WT, NT, false>(work, a.twf + S::TW2_OFF);
@@ -330,6 +351,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       __syncthreads();
     }
+    tile = s_next;
   }
 }
 
@@ -537,8 +559,9 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent fused decode with TMA-staged received rows (packed layout:
-// row i of recv holds the symbols of positions[i]; n = L, k <= n/2).  Same
+// Fused decode with TMA-staged received rows (packed layout: row i of recv
+// holds the symbols of positions[i]; n = L, k <= n/2).  One CTA per tile of WT
+// codewords, tiles of CTAs not yet launched taken over as in k_encode_tma.  Same
 // transform sequence as k_decode; pass 1 gathers u[z] = v_row(z) * c_z from the
 // staged [k][WT] tile through pat32[z] = (row << 17) | c_z (c_z = 0: unused).
 // smem: work (Lay WORDS u32) | stage (rows_staged * WT u32) | mbarrier.
@@ -565,33 +588,42 @@ __global__ void __launch_bounds__(NT, 1)
   using Y = Lay<S, WT>;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
   extern __shared__ __align__(128) uint4 smem_raw[];
+  __shared__ int s_next;
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)rows_staged * WT);
+  uint64_t* cbar = bar + 1;
+  uint4* resp = reinterpret_cast<uint4*>(bar + 2);
   const int ntiles = (a.W + WT - 1) / WT;
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
   const uint32_t* __restrict__ ahat = a.ahat;
-  if (threadIdx.x == 0) mbar_init(bar, 1);
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init(cbar, 1);
+  }
   __syncthreads();
-  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+  if (threadIdx.x == 0 && tile < ntiles) {
     mbar_expect_tx(bar, tx_bytes);
     for (int bx = 0; bx < nbox; ++bx)
-      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, (int)blockIdx.x * WT,
-                  bx * box_rows, bar);
+      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, tile * WT, bx * box_rows, bar);
+    clc_request(resp, cbar);
   }
-  uint32_t parity = 0;
+  uint32_t parity = 0, cphase = 0;
+  bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
   LoadStaged<WT> load{stage, pat32, 0u};
   StoreOut16<WT> store = StoreOut16<WT>::make(a);
   NopStore nop;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  while (tile < ntiles) {
     const bool ok = mbar_wait(bar, parity);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(a.status, ST_TIMEOUT);
-        mbar_wait(bar, parity);
+        mbar_wait(bar, parity);  // let the copy in flight land before exiting
+        if (pending) mbar_wait(cbar, cphase);
       }
       return;
     }
@@ -600,12 +632,22 @@ __global__ void __launch_bounds__(NT, 1)
     // D1 pass 1 (root r^-1) from the stage
     dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
     __syncthreads();
-    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
-      fence_proxy_async();
-      mbar_expect_tx(bar, tx_bytes);
-      for (int bx = 0; bx < nbox; ++bx)
-        tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, (tile + (int)gridDim.x) * WT,
-                    bx * box_rows, bar);
+    if (threadIdx.x == 0) {
+      // the stage is free: take over a pending CTA's tile and prefetch it
+      int nxt = clc_take(resp, cbar, cphase);
+      pending = false;
+      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+      if (nxt >= 0 && nxt < ntiles) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, tx_bytes);
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, nxt * WT, bx * box_rows, bar);
+        clc_request(resp, cbar);
+        pending = true;
+      } else {
+        nxt = ntiles;
+      }
+      s_next = nxt;
     }
     if constexpr (S::NP == 3) {
       dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
@@ -664,6 +706,7 @@ __global__ void __launch_bounds__(NT, 1)
     }
     dif_last<S, WT, NT, true>(sm, store);
     __syncthreads();
+    tile = s_next;
   }
   if (load.vmax > 65536u) atomicOr(a.status, ST_RANGE);
   store.flush();
@@ -863,67 +906,70 @@ __global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Log-domain pattern build for n = L <= tile limit (see pattern.cu for the
-// identities).  k_plan_spec: one CTA resets the position table, scatters the
-// first k positions (their received-row index and the indicator 1_R) and
-// writes spec = FNT_n(1_R).  k_plan_conv: CTA t multiplies spec by the
-// transform of digit t of the reversed log table and writes its inverse FNT,
-// conv[j][t] = (1_R * g'_t)[j], exact integers below p.
-// smem: work (Lay<S,1> WORDS) | indicator (L words).
+// Log-domain pattern build for n = L <= tile limit, one launch (see pattern.cu
+// and logplan.cuh for the identities).  CTA t < D: scatters the first k
+// positions into shared memory (received-row index + 1, 0 = erased),
+// transforms the indicator 1_R (spec = FNT_n(1_R), every CTA for itself),
+// multiplies by the transform of digit t of the reversed log table and writes
+// conv[j][t] = (1_R * g'_t)[j], exact integers below p.  CTA 0 also writes the
+// position table.  The last CTA to finish (counter `done`, left at zero for the
+// next build) turns the digits into weights, pat32 and ahat (or aval).
+// smem: work (Lay<S,1> WORDS) | row index / spec (L words).
 // ---------------------------------------------------------------------------
 template <class S, int NT>
-__global__ void __launch_bounds__(NT) k_plan_spec(KArgs a, const uint32_t* __restrict__ pos,
-                                                  uint32_t* __restrict__ spec) {
-  using Y = Lay<S, 1>;
+__global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
+  static_assert(S::NP >= 2, "");
+  constexpr int L = S::L, PER = 8;
   extern __shared__ uint4 smem_raw[];
+  __shared__ int s_last;
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* ind = sm + Y::WORDS;
-  uint2* pat = const_cast<uint2*>(a.pat);
-  for (int z = threadIdx.x; z < S::L; z += NT) {
-    ind[z] = 0u;
-    pat[z] = make_uint2(0xFFFFFFFFu, 0u);
+  uint32_t* ind = sm + Lay<S, 1>::WORDS;
+  const int t = blockIdx.x, k = pa.k;
+  for (int z = threadIdx.x; z < L; z += NT) ind[z] = 0u;
+  __syncthreads();
+  for (int i0 = 0; i0 < k; i0 += NT * PER) {
+    uint32_t zz[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int i = i0 + u * NT + (int)threadIdx.x;
+      zz[u] = i < k ? __ldg(pa.pos + i) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (zz[u] < (uint32_t)L) ind[zz[u]] = (uint32_t)(i0 + u * NT + (int)threadIdx.x) + 1u;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < a.k; i += NT) {
-    const uint32_t z = pos[i];
-    ind[z] = 1u;
-    pat[z].x = (uint32_t)i;
-  }
-  __syncthreads();
+  if (t == 0)
+    for (int z = threadIdx.x; z < L; z += NT) {
+      const uint32_t r = ind[z];
+      pa.pat[z] = make_uint2(r ? r - 1u : 0xFFFFFFFFu, 0u);
+    }
+  // spec = FNT_n(1_R), left in ind[] (natural order) once pass 1 has read it
   struct LoadInd {
     const uint32_t* ind;
-    __device__ uint32_t operator()(int i, int) const { return ind[i]; }
-  } ld{ind};
+    __device__ uint32_t operator()(int i, int) const { return ind[i] != 0u ? 1u : 0u; }
+  } ld1{ind};
   struct StoreSpec {
     uint32_t* spec;
     __device__ void operator()(int j, int, uint32_t v) const { spec[j] = m_to_p(v); }
-  } st{spec};
-  dif_first<S, 1, NT, false>(sm, a.twf, ld, st);
-  if constexpr (S::NP >= 2) {
+  } st1{ind};
+  dif_first<S, 1, NT, false>(sm, pa.twf, ld1, st1);
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, 1, NT, false>(sm, pa.twf + S::TW2_OFF);
     __syncthreads();
-    if constexpr (S::NP == 3) {
-      dif_mid<S, 1, NT, false>(sm, a.twf + S::TW2_OFF);
-      __syncthreads();
-    }
-    dif_last<S, 1, NT, false>(sm, st);
   }
-}
-
-template <class S, int NT>
-__global__ void __launch_bounds__(NT) k_plan_conv(KArgs a, const uint32_t* __restrict__ spec,
-                                                  const uint32_t* __restrict__ ghat, int D,
-                                                  uint32_t* __restrict__ conv) {
-  extern __shared__ uint4 smem_raw[];
-  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
-  const int t = blockIdx.x;
+  dif_last<S, 1, NT, false>(sm, st1);
+  __syncthreads();
+  // conv[.][t] = n^-1 IFNT(spec * ghat[.][t])
   struct LoadProd {
     const uint32_t* spec;
     const uint32_t* ghat;
     int D, t;
     __device__ uint32_t operator()(int j, int) const {
-      return m_mul(__ldg(ghat + (size_t)j * D + t), __ldg(spec + j));
+      return m_mul(__ldg(ghat + (size_t)j * D + t), spec[j]);
     }
-  } ld{spec, ghat, D, t};
+  } ld2{ind, pa.ghat, pa.D, t};
   struct StoreConv {
     uint32_t* conv;
     int D, t;
@@ -931,16 +977,24 @@ __global__ void __launch_bounds__(NT) k_plan_conv(KArgs a, const uint32_t* __res
     __device__ void operator()(int j, int, uint32_t v) const {
       conv[(size_t)j * D + t] = m_to_p(m_mul(v, ninv));
     }
-  } st{conv, D, t, a.scale};
-  dif_first<S, 1, NT, true>(sm, a.twi, ld, st);
-  if constexpr (S::NP >= 2) {
+  } st2{pa.conv, pa.D, t, pa.ninv};
+  dif_first<S, 1, NT, true>(sm, pa.twi, ld2, st2);
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, 1, NT, true>(sm, pa.twi + S::TW2_OFF);
     __syncthreads();
-    if constexpr (S::NP == 3) {
-      dif_mid<S, 1, NT, true>(sm, a.twi + S::TW2_OFF);
-      __syncthreads();
-    }
-    dif_last<S, 1, NT, true>(sm, st);
   }
+  dif_last<S, 1, NT, true>(sm, st2);
+  // the last CTA to get here combines the digits of all CTAs
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(pa.done, 1u) == (uint32_t)pa.D - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const LogFinal f{pa.conv, pa.D, pa.b, L, k, pa.exp3, pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat};
+  lg_final_block<L, NT>(f);
+  if (threadIdx.x == 0) *pa.done = 0u;
 }
 
 // ---------------------------------------------------------------------------

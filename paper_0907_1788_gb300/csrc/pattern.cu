@@ -15,6 +15,7 @@
 
 #include "field.cuh"
 #include "kargs.h"
+#include "logplan.cuh"
 
 namespace fntrs {
 
@@ -168,36 +169,11 @@ __global__ void k_lg_mul(const uint32_t* __restrict__ spec, const uint32_t* __re
   P[t] = m_to_p(m_mul(ghat[t], m_to_p(spec[j])));
 }
 
-// weights of received positions; A(r^j) of the others (Aval) and, unless the
+// weights of received positions; A(r^j) of the others (aval) and, unless the
 // step-6 product is split, ahat_j = n^-1 (A(r^j) - r^(jk)) = n^-1 FNT(A mod x^k)_j.
-__global__ void k_lg_final(const uint32_t* __restrict__ conv, int D, int b, int n, int k,
-                           const uint32_t* __restrict__ exp3, uint32_t ninv, uint2* pat,
-                           uint32_t* __restrict__ pat32, uint32_t* __restrict__ aval,
-                           uint32_t* __restrict__ ahat) {
+__global__ void k_lg_final(LogFinal f) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  uint32_t S = 0u;
-  for (int t = 0; t < D; ++t) S += conv[(size_t)j * D + t] << (b * t);
-  const uint32_t step = 65536u / (uint32_t)n;
-  const uint32_t jl = (uint32_t)j * step;  // log_3 r^j
-  const bool received = pat[j].x != 0xFFFFFFFFu;
-  uint32_t A = 0u;
-  if (received) {
-    const uint32_t ld = (jl * (uint32_t)(k - 1) + S) & 0xFFFFu;  // log A'(r^j)
-    // c = -r^-j / A'(r^j) = -3^-(jl + ld)
-    const uint32_t e = (0u - (jl + ld)) & 0xFFFFu;
-    const uint32_t c = kP - exp3[e];
-    pat[j].y = c;
-    pat32[j] = (pat[j].x << 17) | c;
-  } else {
-    pat32[j] = 0u;
-    A = exp3[(jl * (uint32_t)k + S) & 0xFFFFu];
-  }
-  if (aval) aval[j] = A;
-  if (ahat) {
-    const uint32_t rjk = exp3[(jl * (uint32_t)k) & 0xFFFFu];
-    ahat[j] = p_mul(m_to_p(m_sub(A, rjk)), ninv);
-  }
+  if (j < f.n) lg_final_one(f, j, f.pat[j].x);
 }
 
 // coefficient halves of A (k > n/2): M[j][0] = A_j (j < h), M[j][1] = A_(h+j) (j < k-h);
@@ -259,8 +235,8 @@ void launch_lg_mul(const uint32_t* spec, const uint32_t* ghat, int D, int n, uin
 void launch_lg_final(const uint32_t* conv, int D, int b, int n, int k, const uint32_t* exp3,
                      uint32_t ninv, uint2* pat, uint32_t* pat32, uint32_t* aval, uint32_t* ahat,
                      cudaStream_t st) {
-  k_lg_final<<<blocks_for(n, 256), 256, 0, st>>>(conv, D, b, n, k, exp3, ninv, pat, pat32, aval,
-                                                  ahat);
+  const LogFinal f{conv, D, b, n, k, exp3, ninv, pat, pat32, aval, ahat};
+  k_lg_final<<<blocks_for(n, 256), 256, 0, st>>>(f);
   count_launch();
 }
 void launch_lg_halves(const uint32_t* coef, int n, int k, uint32_t* M, cudaStream_t st) {

@@ -338,9 +338,45 @@ size_t pattern_scratch_words(uint32_t n, uint32_t k) {
   return std::max(tree, lg);
 }
 
+int alloc_pattern_tables(PatternSlot& sl, size_t n, bool staging) {
+  if (cudaMalloc(&sl.pat, n * sizeof(uint2)) != cudaSuccess ||
+      cudaMalloc(&sl.ahat, n * 4) != cudaSuccess || cudaMalloc(&sl.ahat2, n * 4) != cudaSuccess ||
+      cudaMalloc(&sl.pos_d, n * 4) != cudaSuccess || cudaMalloc(&sl.pat32, n * 4) != cudaSuccess ||
+      cudaMalloc(&sl.done, 4) != cudaSuccess || cudaMemset(sl.done, 0, 4) != cudaSuccess)
+    return FNT_RS_E_CUDA;
+  if (staging && (cudaMallocHost(&sl.pos_h, n * 4) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&sl.staged, cudaEventDisableTiming) != cudaSuccess))
+    return FNT_RS_E_CUDA;
+  if (staging) {
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, sl.pos_h, 0) == cudaSuccess)
+      sl.pos_map = static_cast<const uint32_t*>(dp);
+    else
+      cudaGetLastError();  // not mapped: positions go through pos_d
+  }
+  return FNT_RS_OK;
+}
+
+void free_pattern_tables(PatternSlot& sl) {
+  cudaFree(sl.pat);
+  cudaFree(sl.ahat);
+  cudaFree(sl.ahat2);
+  cudaFree(sl.pos_d);
+  cudaFree(sl.pat32);
+  cudaFree(sl.done);
+  if (sl.pos_h) cudaFreeHost(sl.pos_h);
+  if (sl.staged) cudaEventDestroy(sl.staged);
+  sl = PatternSlot{};
+}
+
 // Log-domain build of the pattern tables (see pattern.cu); `scratch` holds
 // pattern_scratch_words(n, k) words (the plan's own scratch when null).
-int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32_t* scratch) {
+bool fused_plan_applies(const fnt_rs_plan_s* p) {
+  return !p->plan_tree && !p->split && tile_ops((int)p->n).plan_fused != nullptr;
+}
+
+int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32_t* scratch,
+                      const uint32_t* pos) {
   const int n = (int)p->n, k = (int)p->k, D = p->lg_D;
   uint32_t* ind = scratch ? scratch : p->pscratch;
   uint32_t* spec = ind + n;
@@ -353,31 +389,39 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32
   uint32_t* work = conv + 16 * (size_t)n;
   int rc;
   const TileOps& ops = tile_ops(n);
-  if (!p->split && ops.plan_spec) {
-    // fused: one CTA for the indicator spectrum, one CTA per digit convolution
-    KArgs a;
-    a.n = n;
-    a.k = k;
-    a.L = n;
-    a.pat = sl.pat;
-    a.twf = p->tn.twf;
-    a.twi = p->tn.twi;
-    a.scale = p->ninv;
-    ops.plan_spec(a, sl.pos_d, spec, st);
-    ops.plan_conv(a, spec, p->ghat, D, conv, st);
+  if (!p->split && ops.plan_fused) {
+    PlanArgs pa;
+    pa.k = k;
+    pa.D = D;
+    pa.b = p->lg_b;
+    pa.ninv = p->ninv;
+    pa.twf = p->tn.twf;
+    pa.twi = p->tn.twi;
+    pa.pos = pos ? pos : sl.pos_d;
+    pa.ghat = p->ghat;
+    pa.exp3 = p->exp3;
+    pa.conv = conv;
+    pa.pat = sl.pat;
+    pa.pat32 = sl.pat32;
+    pa.aval = p->blocked ? aval : nullptr;
+    pa.ahat = p->blocked ? nullptr : sl.ahat;
+    pa.done = sl.done;
+    ops.plan_fused(pa, st);
+    if (!p->blocked) return cuda_ok(cudaGetLastError());
   } else {
     launch_lg_init(sl.pat, ind, n, st);
     launch_lg_scatter(sl.pos_d, k, sl.pat, ind, st);
     if ((rc = run_fnt_default(n, ind, 1, spec, 1, 1, false, 1, work, st))) return rc;
     launch_lg_mul(spec, p->ghat, D, n, P, st);
     if ((rc = run_fnt_default(n, P, D, conv, D, D, true, 1, work, st))) return rc;
-  }
-  if (!p->blocked) {
-    launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, nullptr, sl.ahat,
+    if (!p->blocked) {
+      launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, nullptr,
+                      sl.ahat, st);
+      return cuda_ok(cudaGetLastError());
+    }
+    launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, aval, nullptr,
                     st);
-    return cuda_ok(cudaGetLastError());
   }
-  launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, aval, nullptr, st);
   if ((rc = run_fnt_default(n, aval, 1, coef, 1, 1, true, 1, work, st))) return rc;
   launch_lg_halves(coef, n, k, M2, st);
   if ((rc = run_fnt_default(n, M2, 2, E2, 2, 2, false, 1, work, st))) return rc;
@@ -480,13 +524,21 @@ static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, c
   }
   PatternSlot& sl = p->slots[victim];
   sl.valid = false;
-  // the slot's staging buffer may still feed its previous upload
+  // the slot's staging buffer may still be read by its previous build
   if ((rc = cuda_ok(cudaEventSynchronize(sl.staged)))) return rc;
   std::memcpy(sl.pos_h, key.data(), key.size() * 4);
-  if ((rc = cuda_ok(cudaMemcpyAsync(sl.pos_d, sl.pos_h, key.size() * 4, cudaMemcpyHostToDevice, st))))
-    return rc;
-  if ((rc = cuda_ok(cudaEventRecord(sl.staged, st)))) return rc;
-  if ((rc = p->plan_tree ? build_pattern(p, sl, st) : build_pattern_log(p, sl, st))) return rc;
+  if (sl.pos_map && fused_plan_applies(p)) {
+    // the one-launch build reads the positions from the pinned buffer itself,
+    // so it does not queue behind a copy
+    if ((rc = build_pattern_log(p, sl, st, nullptr, sl.pos_map))) return rc;
+    if ((rc = cuda_ok(cudaEventRecord(sl.staged, st)))) return rc;
+  } else {
+    if ((rc = cuda_ok(cudaMemcpyAsync(sl.pos_d, sl.pos_h, key.size() * 4,
+                                      cudaMemcpyHostToDevice, st))))
+      return rc;
+    if ((rc = cuda_ok(cudaEventRecord(sl.staged, st)))) return rc;
+    if ((rc = p->plan_tree ? build_pattern(p, sl, st) : build_pattern_log(p, sl, st))) return rc;
+  }
   sl.key.swap(key);
   sl.valid = true;
   sl.last_use = p->clock;
@@ -497,7 +549,7 @@ static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, c
 // ---------------------------------------------------------------------------
 // encode / decode / fnt dispatch
 // ---------------------------------------------------------------------------
-// Persistent TMA-staged encode; returns 1 if it was not applicable.
+// TMA-staged encode (cluster-launch-control tile scheduling); returns 1 if it was not applicable.
 static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                       size_t ld_enc, size_t W, cudaStream_t st) {
   if (p->no_tma || p->enc_L == 0 || p->u != 1) return 1;
@@ -532,7 +584,7 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   t.twc = p->twc;
   t.rows_staged = rows_staged;
   t.box_rows = box_rows;
-  t.grid = std::min(ntiles, p->sms);
+  t.grid = ntiles;  // one CTA per tile; running CTAs take over pending ones
   t.map = &map;
   if (launch_encode_tma(L, C, a, t, st) != 0) return 1;
   return cuda_ok(cudaGetLastError());
@@ -592,7 +644,8 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
   return cuda_ok(cudaGetLastError());
 }
 
-// Persistent TMA-staged decode (packed rows, n <= tile limit, k <= n/2);
+// TMA-staged decode (one CTA per tile, cluster launch control; packed rows,
+// n <= tile limit, k <= n/2);
 // returns 1 if not applicable.
 static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                       size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
@@ -630,7 +683,7 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   t.pat32 = sl.pat32;
   t.rows_staged = rows_staged;
   t.box_rows = box_rows;
-  t.grid = std::min((int)((W + WT - 1) / WT), p->sms);
+  t.grid = (int)((W + WT - 1) / WT);  // one CTA per tile (see clc_take)
   t.map = &map;
   if (launch_decode_tma(L, a, t, st) != 0) return 1;
   return cuda_ok(cudaGetLastError());
@@ -870,16 +923,8 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
     return fail(FNT_RS_E_CUDA);
   p->pscratch_words = pattern_scratch_words(n, k);
   if (cudaMalloc(&p->pscratch, p->pscratch_words * 4) != cudaSuccess) return fail(FNT_RS_E_CUDA);
-  for (auto& sl : p->slots) {
-    if (cudaMalloc(&sl.pat, (size_t)n * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&sl.ahat, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&sl.ahat2, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&sl.pos_d, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&sl.pat32, (size_t)n * 4) != cudaSuccess ||
-        cudaMallocHost(&sl.pos_h, (size_t)n * 4) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.staged, cudaEventDisableTiming) != cudaSuccess)
-      return fail(FNT_RS_E_CUDA);
-  }
+  for (auto& sl : p->slots)
+    if ((rc = alloc_pattern_tables(sl, n, true))) return fail(rc);
   if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return fail(FNT_RS_E_CUDA);
   *out = p;
   return FNT_RS_OK;
@@ -892,15 +937,7 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   cudaFree(p->pscratch);
   cudaFree(p->twc);
   cudaFree(p->ghat);
-  for (auto& sl : p->slots) {
-    cudaFree(sl.pat);
-    cudaFree(sl.ahat);
-    cudaFree(sl.ahat2);
-    cudaFree(sl.pos_d);
-    cudaFree(sl.pat32);
-    if (sl.pos_h) cudaFreeHost(sl.pos_h);
-    if (sl.staged) cudaEventDestroy(sl.staged);
-  }
+  for (auto& sl : p->slots) free_pattern_tables(sl);
   delete p;
 }
 

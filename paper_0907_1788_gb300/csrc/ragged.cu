@@ -58,13 +58,7 @@ static int run_group(RaggedGroup& rg, void* ws, cudaStream_t st) {
   return do_decode_tables(p, rg.tab, g.enc, g.ld_enc, g.out, g.ld_out, g.W, ws, st, 1);
 }
 
-static void free_group(RaggedGroup& rg) {
-  cudaFree(rg.tab.pat);
-  cudaFree(rg.tab.pat32);
-  cudaFree(rg.tab.ahat);
-  cudaFree(rg.tab.ahat2);
-  cudaFree(rg.tab.pos_d);
-}
+static void free_group(RaggedGroup& rg) { free_pattern_tables(rg.tab); }
 
 }  // namespace fntrs
 
@@ -120,13 +114,7 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     fnt_rs_plan_s* p = rg.plan;
     int rc = validate_positions(p, rg.g.positions, rg.g.npos);
     if (rc) return fail(rc);
-    const size_t n = p->n;
-    if (cudaMalloc(&rg.tab.pat, n * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&rg.tab.pat32, n * 4) != cudaSuccess ||
-        cudaMalloc(&rg.tab.ahat, n * 4) != cudaSuccess ||
-        cudaMalloc(&rg.tab.ahat2, n * 4) != cudaSuccess ||
-        cudaMalloc(&rg.tab.pos_d, n * 4) != cudaSuccess)
-      return fail(FNT_RS_E_CUDA);
+    if ((rc = alloc_pattern_tables(rg.tab, p->n, false))) return fail(rc);
     if (cudaMemcpy(rg.tab.pos_d, rg.g.positions, (size_t)p->k * 4, cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return fail(FNT_RS_E_CUDA);

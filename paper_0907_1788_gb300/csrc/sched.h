@@ -42,10 +42,8 @@ struct TileOps {
   Launch decode = nullptr;      // fused decode, k <= n/2
   Launch decode_split = nullptr;  // fused decode, k > n/2
   Launch poly_level = nullptr;  // product-tree level (L = 2d)
-  // log-domain pattern build (n = L): spectrum of the indicator, digit convolutions
-  void (*plan_spec)(const KArgs&, const uint32_t* pos, uint32_t* spec, cudaStream_t) = nullptr;
-  void (*plan_conv)(const KArgs&, const uint32_t* spec, const uint32_t* ghat, int D,
-                    uint32_t* conv, cudaStream_t) = nullptr;
+  // log-domain pattern build (n = L) in one launch of D CTAs
+  void (*plan_fused)(const PlanArgs&, cudaStream_t) = nullptr;
 };
 
 // Registry filled by the instantiation units.
@@ -54,7 +52,7 @@ void register_tile_ops_small();
 void register_tile_ops_mid();
 void register_tile_ops_big();
 
-// Persistent TMA-staged encode for tile length L (C = 1) or n = 2L (C = 2).
+// TMA-staged encode for tile length L (C = 1) or n = 2L (C = 2).
 // Returns -1 if the configuration has no instantiation.
 struct TmaEncodeArgs {
   const uint32_t* twc;
@@ -63,7 +61,7 @@ struct TmaEncodeArgs {
 };
 int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 
-// Persistent TMA-staged decode (n = L <= tile limit, k <= n/2, packed rows).
+// TMA-staged decode (n = L <= tile limit, k <= n/2, packed rows).
 struct TmaDecodeArgs {
   const uint32_t* pat32;
   int rows_staged, box_rows, grid;

@@ -205,12 +205,7 @@ static int get_plan(fnt_rs_server_s* s, uint32_t n, uint32_t k, PlanRes** out) {
   pr->plan = h;
   for (uint32_t i = 0; i < s->pats_per_plan; ++i) {
     auto* e = new PatEntry();
-    if (cudaMalloc(&e->tab.pat, (size_t)n * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&e->tab.pat32, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&e->tab.ahat, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&e->tab.ahat2, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&e->tab.pos_d, (size_t)n * 4) != cudaSuccess ||
-        cudaMallocHost(&e->tab.pos_h, (size_t)n * 4) != cudaSuccess ||
+    if (alloc_pattern_tables(e->tab, n, true) != FNT_RS_OK ||
         cudaEventCreateWithFlags(&e->built, cudaEventDisableTiming) != cudaSuccess)
       return FNT_RS_E_CUDA;
     pr->pool.push_back(e);
@@ -565,12 +560,7 @@ void fnt_rs_server_destroy(fnt_rs_server s) {
   }
   for (auto& kv : s->plans) {
     for (auto* e : kv.second->pool) {
-      cudaFree(e->tab.pat);
-      cudaFree(e->tab.pat32);
-      cudaFree(e->tab.ahat);
-      cudaFree(e->tab.ahat2);
-      cudaFree(e->tab.pos_d);
-      if (e->tab.pos_h) cudaFreeHost(e->tab.pos_h);
+      free_pattern_tables(e->tab);
       if (e->built) cudaEventDestroy(e->built);
       delete e;
     }

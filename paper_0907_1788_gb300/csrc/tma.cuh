@@ -3,6 +3,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <cuda/ptx>
+
 namespace fntrs {
 
 // Upper bound on mbarrier polls before a wait gives up (the kernel then
@@ -58,5 +60,41 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+
+// ---------------------------------------------------------------------------
+// Cluster launch control (sm_100 and later).  The TMA kernels are launched
+// with one CTA per tile; a running CTA asks the hardware to cancel the launch
+// of a CTA of the same grid that has not started yet and then processes that
+// CTA's tile itself (prefetching it while it finishes the current one).  Every
+// tile is thus processed exactly once, by its own CTA if that CTA is launched
+// or else by the CTA whose request cancelled it, and CTAs that start late
+// (the SM was busy with another kernel) simply take fewer tiles.  After a
+// request that cancelled nothing, no further request is made.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void clc_request(uint4* resp, uint64_t* bar) {
+  cuda::ptx::clusterlaunchcontrol_try_cancel(resp, bar);
+  mbar_expect_tx(bar, 16);
+}
+
+constexpr int kClcNone = -1;     // the request cancelled nothing
+constexpr int kClcTimeout = -2;  // the response did not arrive within the bound
+
+// Waits for the outstanding request (phase `phase` of `bar`) and returns the
+// x index of the cancelled CTA, kClcNone or kClcTimeout.
+__device__ __forceinline__ int clc_take(const uint4* resp, uint64_t* bar, uint32_t& phase) {
+  if (!mbar_wait(bar, phase)) return kClcTimeout;
+  phase ^= 1u;
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"(smem_u32(resp))
+               : "memory");
+  if (!cuda::ptx::clusterlaunchcontrol_query_cancel_is_canceled(r)) return kClcNone;
+  return (int)cuda::ptx::clusterlaunchcontrol_query_cancel_get_first_ctaid_x<uint32_t>(r);
+}
+
+// Shared-memory bytes after a TMA kernel's stage: the TMA barrier, the
+// cancel barrier and the 16-byte cancel response.
+constexpr int kSchedBytes = 64;
 
 }  // namespace fntrs
