@@ -255,9 +255,10 @@ def ragged_measure(pkg, dev, budget_bytes=6 << 30, nstreams=16):
                        "that fit one 6 GB wave; each group = encode + pattern build + decode")}
 
 
-def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30):
+def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30, patterns_per_shape=64):
     """cfg5 trace head: continuous batching server vs one request at a time."""
-    reqs = synth.serving_requests(seed=5, rate_per_s=rate, duration_s=count / rate * 2)[:count]
+    reqs = synth.serving_requests(seed=5, rate_per_s=rate, duration_s=count / rate * 2,
+                                  patterns_per_shape=patterns_per_shape)[:count]
     trace = []
     for q in reqs:
         d = dict(op=q["op"], n=q["n"], k=q["k"], W=q["W"], seed=q["seed"])
@@ -288,8 +289,24 @@ def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30):
                          "kind": "one request at a time, plan + pattern built per request"},
             "budget_gb": budget / 2**30, "streams": 16,
             "config": ("seed-5 Poisson trace (n = 2^U{9..16}, rho in {1/2,3/4}, packets "
-                       "2^U{10..14} B, half decode with 64 recurring patterns per shape), first "
-                       f"{len(trace)} requests; inputs generated on the device")}
+                       f"2^U{{10..14}} B, half decode with {patterns_per_shape} recurring patterns "
+                       f"per shape), first {len(trace)} requests; inputs generated on the device")}
+
+
+def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
+    """The cfg5 arrival rates, each on the head of its seeded trace, plus a
+    fresh-pattern variant (every decode request brings a new erasure pattern)."""
+    runs = [serving_measure(pkg, rate=r, count=count) for r in rates]
+    fresh = serving_measure(pkg, rate=rates[0], count=count, patterns_per_shape=1 << 30)
+    keep = ("rate_per_s", "requests", "rejected", "p50_ms", "p99_ms", "achieved_gbs")
+    out = dict(runs[0])
+    out["sweep"] = [dict({k: r[k] for k in keep},
+                         baseline={k: r["baseline"][k] for k in ("p50_ms", "p99_ms", "achieved_gbs")})
+                    for r in runs]
+    out["fresh_patterns"] = dict({k: fresh[k] for k in keep},
+                                 baseline={k: fresh["baseline"][k]
+                                           for k in ("p50_ms", "p99_ms", "achieved_gbs")})
+    return out
 
 
 def run_reference(args):
@@ -510,7 +527,7 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_extras:
         line["ragged"] = ragged_measure(pkg, dev)
-        line["serving"] = serving_measure(pkg)
+        line["serving"] = serving_sweep(pkg, count=args.serving_requests)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -526,6 +543,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged and serving runs")
+    ap.add_argument("--serving-requests", type=int, default=300,
+                    help="requests replayed per arrival rate in the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

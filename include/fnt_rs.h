@@ -219,7 +219,11 @@ int fnt_rs_status(fnt_rs_plan plan, void* stream);
  * pointers except `positions` (host, copied at creation).  The library owns
  * one plan per distinct (n, k), each decode group's pattern tables and the
  * split-transform workspace; creation runs the batch once (uncaptured) and
- * captures it into one CUDA graph over up to `nstreams` streams.
+ * captures it into one CUDA graph.  In that graph every group with
+ * 256 <= n <= 8192 runs inside one launch of a persistent kernel (its CTAs
+ * take the groups' encode tiles, pattern builds and decode tiles from one
+ * work list); the other groups keep per-group launches spread over up to
+ * `nstreams` streams.  Groups must not share output buffers.
  */
 typedef struct fnt_rs_group_s {
   uint32_t n, k;
@@ -244,7 +248,8 @@ int fnt_rs_ragged_run(fnt_rs_ragged r, void* stream);
 int fnt_rs_ragged_run_plain(fnt_rs_ragged r, void* stream);
 /* ORs the status words of the batch's plans (synchronises `stream`). */
 int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream);
-/* {groups, plans, streams}; returns the number of ints written. */
+/* {groups, plans, streams, groups in the persistent kernel, its work items};
+ * returns the number of ints written (at most cap). */
 int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap);
 void fnt_rs_ragged_destroy(fnt_rs_ragged r);
 

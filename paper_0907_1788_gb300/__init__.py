@@ -196,9 +196,10 @@ def fnt_rs_ragged_status(r, stream=None) -> int:
 
 
 def fnt_rs_ragged_info(r) -> dict:
-    buf = (ctypes.c_int * 3)()
-    m = load().fnt_rs_ragged_info(r, buf, 3)
-    return dict(zip(["groups", "plans", "streams"], [int(buf[i]) for i in range(m)]))
+    buf = (ctypes.c_int * 5)()
+    m = load().fnt_rs_ragged_info(r, buf, 5)
+    return dict(zip(["groups", "plans", "streams", "persistent_groups", "persistent_items"],
+                    [int(buf[i]) for i in range(m)]))
 
 
 def fnt_rs_ragged_destroy(r):

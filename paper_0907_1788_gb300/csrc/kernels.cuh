@@ -22,13 +22,13 @@ struct LoadSrcFold {
   size_t ld;
   const uint32_t* powf;
   int col0, W, k, L, C, cc, eC, nmask;
-  static __device__ __forceinline__ LoadSrcFold make(const KArgs& a) {
+  static __device__ __forceinline__ LoadSrcFold make(const KArgs& a, int tx, int ty) {
     int lc = 0;
     for (int c = a.C; c > 1; c >>= 1) lc += 1;  // log2(C)
     // e_C for C = 2,4,8,16: 16, 24, 12, 6  (2^e_C = 3^(65536/C) mod p)
     const int eC = lc == 0 ? 0 : (lc == 1 ? 16 : (lc == 2 ? 24 : (lc == 3 ? 12 : 6)));
     return LoadSrcFold{static_cast<const uint16_t*>(a.in), a.ld_in, a.powf,
-                       (int)blockIdx.x * WT, a.W, a.k, a.L, a.C, (int)blockIdx.y, eC, a.n - 1};
+                       tx * WT, a.W, a.k, a.L, a.C, ty, eC, a.n - 1};
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) const {
     const int col = col0 + c;
@@ -44,7 +44,7 @@ struct LoadSrcFold {
   }
 };
 
-// Rows [row0, row0 + L) of a u32 matrix (row0 = blockIdx.y * L).
+// Rows [row0, row0 + L) of a u32 matrix (row0 = ty * L for tile row ty).
 template <int WT>
 struct LoadRows32 {
   const uint32_t* in;
@@ -52,9 +52,9 @@ struct LoadRows32 {
   size_t row0;
   int col0, W;
   uint32_t rmul, nmask;
-  static __device__ __forceinline__ LoadRows32 make(const KArgs& a) {
-    return LoadRows32{static_cast<const uint32_t*>(a.in), a.ld_in, (size_t)blockIdx.y * a.L,
-                      (int)blockIdx.x * WT, a.W, a.in_row_mul, (uint32_t)a.n - 1u};
+  static __device__ __forceinline__ LoadRows32 make(const KArgs& a, int tx, int ty) {
+    return LoadRows32{static_cast<const uint32_t*>(a.in), a.ld_in, (size_t)ty * a.L,
+                      tx * WT, a.W, a.in_row_mul, (uint32_t)a.n - 1u};
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) const {
     const int col = col0 + c;
@@ -69,7 +69,9 @@ struct LoadRows32 {
 // u[z] = v_i * c_i at z = z_i (the first k received positions), 0 elsewhere,
 // with c_i = -r^(-z_i) / A'(r^(z_i)) from the pattern table (weight 0 marks
 // an unused position).  Received values above 65536 are flagged once per
-// thread at the end of the kernel (see flush()).
+// thread at the end of the kernel (see flush()).  Table and received words
+// are read through L2: in a ragged launch they may have been written by
+// other CTAs of the same kernel.
 template <int WT>
 struct LoadRecv {
   const uint32_t* recv;
@@ -78,17 +80,18 @@ struct LoadRecv {
   int* status;
   int col0, W, slots;
   uint32_t bad;
-  static __device__ __forceinline__ LoadRecv make(const KArgs& a) {
-    return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status,
-                    (int)blockIdx.x * WT, a.W, a.slots, 0u};
+  static __device__ __forceinline__ LoadRecv make(const KArgs& a, int tx, int ty) {
+    (void)ty;
+    return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status, tx * WT, a.W,
+                    a.slots, 0u};
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) {
     const int col = col0 + c;
-    const uint2 e = __ldg(pat + i);
+    const uint2 e = __ldcg(pat + i);
     uint32_t v = 0u;
     if (e.y != 0u && col < W) {
       const size_t row = slots ? (size_t)i : (size_t)e.x;
-      v = recv[row * ld + col];
+      v = __ldcg(recv + row * ld + col);
     }
     bad |= v > 65536u ? 1u : 0u;
     return m_mul(v, e.y);
@@ -109,9 +112,9 @@ struct StoreRows32 {
   size_t ld;
   int col0, W, C, cc;
   uint32_t scale, rmul, nmask;
-  static __device__ __forceinline__ StoreRows32 make(const KArgs& a) {
-    return StoreRows32{static_cast<uint32_t*>(a.out), a.ld_out, (int)blockIdx.x * WT, a.W, a.C,
-                       (int)blockIdx.y, a.scale, a.row_mul, (uint32_t)a.n - 1u};
+  static __device__ __forceinline__ StoreRows32 make(const KArgs& a, int tx, int ty) {
+    return StoreRows32{static_cast<uint32_t*>(a.out), a.ld_out, tx * WT, a.W, a.C, ty, a.scale,
+                       a.row_mul, (uint32_t)a.n - 1u};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
     const int col = col0 + c;
@@ -138,8 +141,8 @@ struct StoreLocal {
   KArgs a;
   int col0, j1;
   uint32_t bad;
-  static __device__ __forceinline__ StoreLocal make(const KArgs& a) {
-    return StoreLocal{a, (int)blockIdx.x * WT, (int)blockIdx.y, 0u};
+  static __device__ __forceinline__ StoreLocal make(const KArgs& a, int tx, int ty) {
+    return StoreLocal{a, tx * WT, ty, 0u};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
@@ -196,11 +199,11 @@ __device__ __forceinline__ void flush_if_any(const T&, long) {}
 // grid = (ceil(W / WT), classes or blocks), dynamic smem = Lay WORDS * 4 bytes.
 // ---------------------------------------------------------------------------
 template <class S, int WT, int NT, bool INV, class LD, class ST>
-__global__ void __launch_bounds__(NT) k_tile(KArgs a) {
+__device__ __forceinline__ void tile_body(const KArgs& a, int tx, int ty) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
-  LD load = LD::make(a);
-  ST store = ST::make(a);
+  LD load = LD::make(a, tx, ty);
+  ST store = ST::make(a, tx, ty);
   const uint32_t* tw = INV ? a.twi : a.twf;
   dif_first<S, WT, NT, INV>(sm, tw, load, store);
   if constexpr (S::NP >= 2) {
@@ -212,6 +215,11 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
     dif_last<S, WT, NT, INV>(sm, store);
   }
   flush_if_any(store, 0);
+}
+
+template <class S, int WT, int NT, bool INV, class LD, class ST>
+__global__ void __launch_bounds__(NT) k_tile(KArgs a) {
+  tile_body<S, WT, NT, INV, LD, ST>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -422,9 +430,9 @@ struct StoreOut16 {
   int* status;
   int col0, W, k;
   uint32_t bad;
-  static __device__ __forceinline__ StoreOut16 make(const KArgs& a) {
-    return StoreOut16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, (int)blockIdx.x * WT,
-                      a.W, a.k, 0u};
+  static __device__ __forceinline__ StoreOut16 make(const KArgs& a, int tx, int ty) {
+    (void)ty;
+    return StoreOut16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, tx * WT, a.W, a.k, 0u};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
@@ -445,9 +453,10 @@ struct StoreFirstK16 {
   int* status;
   int col0, W, k;
   uint32_t scale, bad;
-  static __device__ __forceinline__ StoreFirstK16 make(const KArgs& a) {
-    return StoreFirstK16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, (int)blockIdx.x * WT,
-                         a.W, a.k, a.scale, 0u};
+  static __device__ __forceinline__ StoreFirstK16 make(const KArgs& a, int tx, int ty) {
+    (void)ty;
+    return StoreFirstK16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, tx * WT, a.W, a.k,
+                         a.scale, 0u};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
@@ -464,12 +473,12 @@ struct NopStore {
 };
 
 template <class S, int WT, int NT>
-__global__ void __launch_bounds__(NT) k_decode(KArgs a) {
+__device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   using Y = Lay<S, WT>;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a);
-  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
+  StoreOut16<WT> store = StoreOut16<WT>::make(a, tx, 0);
   const uint32_t* __restrict__ ahat = a.ahat;
   if constexpr (S::NP == 1) {
     constexpr int R = S::L, B = ilog2(R);
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
       bitrev_regs<R>(x);
       dft_reg<R, false>(x);
 #pragma unroll
-      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B)));
+      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldcg(ahat + bitrev(q, B)));
       bitrev_regs<R>(x);
       dft_reg<R, true>(x);
 #pragma unroll
@@ -539,7 +548,7 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
         bitrev_regs<R>(x);
         dft_reg<R, false>(x);
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
+        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldcg(ahat + bitrev(q, B) * SP + i2));
         bitrev_regs<R>(x);
         dft_reg<R, true>(x);
         twiddle_regs<R>(x, tw1i + i2 * R);
@@ -556,6 +565,11 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
   }
   load.flush();
   store.flush();
+}
+
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT) k_decode(KArgs a) {
+  decode_body<S, WT, NT>(a, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,7 +629,7 @@ __global__ void __launch_bounds__(NT, 1)
   uint32_t parity = 0, cphase = 0;
   bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
   LoadStaged<WT> load{stage, pat32, 0u};
-  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   NopStore nop;
   while (tile < ntiles) {
     const bool ok = mbar_wait(bar, parity);
@@ -722,10 +736,10 @@ __global__ void __launch_bounds__(NT, 1)
 
 // One codeword per thread, everything in registers (L <= 32).
 template <int L, int WT, int NT>
-__device__ __forceinline__ void decode_split_regs(const KArgs& a) {
+__device__ __forceinline__ void decode_split_regs(const KArgs& a, int tx) {
   constexpr int B = ilog2(L), H = L / 2;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a);
-  StoreOut16<WT> store = StoreOut16<WT>::make(a);
+  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
+  StoreOut16<WT> store = StoreOut16<WT>::make(a, tx, 0);
   for (int c = threadIdx.x; c < WT; c += NT) {
     uint32_t x[L], y[L];
 #pragma unroll
@@ -743,7 +757,7 @@ __device__ __forceinline__ void decode_split_regs(const KArgs& a) {
 #pragma unroll
     for (int q = 0; q < L; ++q) {
       const int i = bitrev(q, B);
-      const uint32_t a0 = __ldg(a.ahat + i), a1 = __ldg(a.ahat2 + i);
+      const uint32_t a0 = __ldcg(a.ahat + i), a1 = __ldcg(a.ahat2 + i);
       const uint32_t s0 = m_to_p(x[q]);
       x[q] = m_mul(s0, a0);
       y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
@@ -766,12 +780,12 @@ __device__ __forceinline__ void decode_split_regs(const KArgs& a) {
 }
 
 template <class S, int WT, int NT>
-__device__ __forceinline__ void decode_split_smem(const KArgs& a) {
+__device__ __forceinline__ void decode_split_smem(const KArgs& a, int tx) {
   using Y = Lay<S, WT>;
   extern __shared__ uint4 smem_raw[];
   uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* Yb = X + Y::WORDS;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a);
+  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
   const int k = a.k;
@@ -836,7 +850,7 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int i = bitrev(q, B) * SP + i2;
-        const uint32_t a0 = __ldg(a.ahat + i), a1 = __ldg(a.ahat2 + i);
+        const uint32_t a0 = __ldcg(a.ahat + i), a1 = __ldcg(a.ahat2 + i);
         const uint32_t s0 = m_to_p(x[q]);
         x[q] = m_mul(s0, a0);
         y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
@@ -865,7 +879,7 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
   {
     constexpr int R = S::RL, HR = R / 2;
     uint16_t* out = static_cast<uint16_t*>(a.out);
-    const int col0 = blockIdx.x * WT;
+    const int col0 = tx * WT;
     for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
       const int c = t % WT, b = t / WT;
       const int col = col0 + c;
@@ -897,12 +911,17 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a) {
 }
 
 template <class S, int WT, int NT>
-__global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
+__device__ __forceinline__ void decode_split_body(const KArgs& a, int tx) {
   if constexpr (S::NP == 1) {
-    decode_split_regs<S::L, WT, NT>(a);
+    decode_split_regs<S::L, WT, NT>(a, tx);
   } else {
-    decode_split_smem<S, WT, NT>(a);
+    decode_split_smem<S, WT, NT>(a, tx);
   }
+}
+
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
+  decode_split_body<S, WT, NT>(a, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -916,15 +935,17 @@ __global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
 // next build) turns the digits into weights, pat32 and ahat (or aval).
 // smem: work (Lay<S,1> WORDS) | row index / spec (L words).
 // ---------------------------------------------------------------------------
+// Digit t's part of the build; returns true in the CTA that finished last
+// (after it has written the tables).
 template <class S, int NT>
-__global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
+__device__ __forceinline__ bool plan_body(const PlanArgs& pa, int t) {
   static_assert(S::NP >= 2, "");
   constexpr int L = S::L, PER = 8;
   extern __shared__ uint4 smem_raw[];
   __shared__ int s_last;
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* ind = sm + Lay<S, 1>::WORDS;
-  const int t = blockIdx.x, k = pa.k;
+  const int k = pa.k;
   for (int z = threadIdx.x; z < L; z += NT) ind[z] = 0u;
   __syncthreads();
   for (int i0 = 0; i0 < k; i0 += NT * PER) {
@@ -990,11 +1011,19 @@ __global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(pa.done, 1u) == (uint32_t)pa.D - 1u;
   __syncthreads();
-  if (!s_last) return;
+  const bool last = s_last;
+  __syncthreads();  // s_last is rewritten by the next build this CTA runs
+  if (!last) return false;
   __threadfence();
   const LogFinal f{pa.conv, pa.D, pa.b, L, k, pa.exp3, pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat};
   lg_final_block<L, NT>(f);
   if (threadIdx.x == 0) *pa.done = 0u;
+  return true;
+}
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
+  plan_body<S, NT>(pa, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,10 +4,13 @@
 // Every group is a full round trip: encode its source (Sec. II.B, e = FNT of
 // the zero-padded source), build its pattern tables (steps 1-3), decode every
 // codeword from the encoded matrix used as the receiver's slot buffer
-// (steps 4-6).  Groups sharing (n, k) share one plan and run in order on one
-// stream (their pattern builds share the plan's scratch); plan classes are
-// spread over several streams by estimated work so that small groups overlap
-// large ones.  The streams are captured into a single graph.
+// (steps 4-6).  Groups with 256 <= n <= 8192 (default root) all run in one
+// launch of the ragged persistent kernel (ragged_kernel.cu), each with its own
+// pattern tables and build scratch.  The other groups (longer codes, through
+// the split transforms) keep per-group launches: groups sharing (n, k) share
+// one plan and run in order on one stream, and plan classes are spread over
+// several streams by estimated work.  The persistent kernel's stream and the
+// others are captured into a single graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +21,8 @@
 #include <vector>
 
 #include "internal.h"
+#include "ragged_dev.h"
+#include "sched.h"
 
 namespace fntrs {
 
@@ -26,6 +31,8 @@ struct RaggedGroup {
   fnt_rs_plan_s* plan = nullptr;
   PatternSlot tab;  // decode groups only
   int stream = 0;
+  bool persistent = false;    // runs in the ragged persistent kernel
+  uint32_t* scratch = nullptr;  // its own pattern-build scratch (persistent decode groups)
 };
 
 }  // namespace fntrs
@@ -43,6 +50,14 @@ struct fnt_rs_ragged_s {
   std::vector<cudaEvent_t> joins;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // ragged persistent kernel
+  RaggedArgs ra{};
+  RaggedGroupDev* d_groups = nullptr;
+  RaggedItem* d_items = nullptr;
+  unsigned* d_counters = nullptr;  // next, enc_done[G], plan_done[G]
+  size_t counter_bytes = 0;
+  int grid = 0;
+  int npersistent = 0;
 };
 
 namespace fntrs {
@@ -58,7 +73,117 @@ static int run_group(RaggedGroup& rg, void* ws, cudaStream_t st) {
   return do_decode_tables(p, rg.tab, g.enc, g.ld_enc, g.out, g.ld_out, g.W, ws, st, 1);
 }
 
-static void free_group(RaggedGroup& rg) { free_pattern_tables(rg.tab); }
+static void free_group(RaggedGroup& rg) {
+  free_pattern_tables(rg.tab);
+  cudaFree(rg.scratch);
+}
+
+static bool persistent_eligible(const fnt_rs_plan_s* p) {
+  return p->n >= (uint32_t)kRaggedMinL && p->n <= (uint32_t)kTileMaxL && p->u == 1 &&
+         !p->plan_tree && fused_plan_applies(p);
+}
+
+// Device group record of a persistent group (same arguments as the per-group
+// generic encode, one-launch pattern build and generic decode).
+static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
+  const fnt_rs_plan_s* p = rg.plan;
+  const fnt_rs_group& g = rg.g;
+  const int n = (int)p->n, k = (int)p->k;
+  RaggedGroupDev d{};
+  d.L = n;
+  d.blocked = p->blocked ? 1 : 0;
+  d.has_plan = g.positions ? 1 : 0;
+  d.enc_tiles = (int)((g.W + ragged_wt_enc(n) - 1) / ragged_wt_enc(n));
+  KArgs& e = d.enc;
+  e.in = g.src;
+  e.ld_in = g.ld_src;
+  e.out = g.enc;
+  e.ld_out = g.ld_enc;
+  e.W = (int)g.W;
+  e.n = n;
+  e.k = k;
+  e.L = n;
+  e.C = 1;
+  e.twf = p->tn.twf;
+  e.twi = p->tn.twi;
+  e.powf = p->tn.powf;
+  e.row_mul = p->uinv;
+  if (!g.positions) return d;
+  KArgs& a = d.dec;
+  a.slots = 1;
+  a.in = g.enc;
+  a.ld_in = g.ld_enc;
+  a.out = g.out;
+  a.ld_out = g.ld_out;
+  a.n = n;
+  a.k = k;
+  a.h = n / 2;
+  a.pat = rg.tab.pat;
+  a.ahat = rg.tab.ahat;
+  a.ahat2 = rg.tab.ahat2;
+  a.status = p->status;
+  a.W = (int)g.W;
+  a.L = n;
+  a.C = 1;
+  a.twf = p->tn.twf;
+  a.twi = p->tn.twi;
+  // scratch: conv [n][D] | aval [n] | coef [n] | halves [n][2] | E [n][2]
+  uint32_t* conv = rg.scratch;
+  uint32_t* aval = conv + (size_t)n * p->lg_D;
+  uint32_t* coef = aval + n;
+  uint32_t* halves = coef + n;
+  uint32_t* E = halves + 2 * (size_t)n;
+  PlanArgs& pa = d.plan;
+  pa.k = k;
+  pa.D = p->lg_D;
+  pa.b = p->lg_b;
+  pa.ninv = p->ninv;
+  pa.twf = p->tn.twf;
+  pa.twi = p->tn.twi;
+  pa.pos = rg.tab.pos_d;
+  pa.ghat = p->ghat;
+  pa.exp3 = p->exp3;
+  pa.conv = conv;
+  pa.pat = rg.tab.pat;
+  pa.pat32 = rg.tab.pat32;
+  pa.aval = p->blocked ? aval : nullptr;
+  pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
+  pa.done = rg.tab.done;
+  d.halves = halves;
+  KArgs& ti = d.tail_inv;
+  ti.in = aval;
+  ti.ld_in = 1;
+  ti.out = coef;
+  ti.ld_out = 1;
+  ti.W = 1;
+  ti.n = n;
+  ti.L = n;
+  ti.C = 1;
+  ti.scale = p->ninv;
+  ti.twf = p->tn.twf;
+  ti.twi = p->tn.twi;
+  KArgs& tf = d.tail_fwd;
+  tf.in = halves;
+  tf.ld_in = 2;
+  tf.out = E;
+  tf.ld_out = 2;
+  tf.W = 2;
+  tf.n = n;
+  tf.L = n;
+  tf.C = 1;
+  tf.twf = p->tn.twf;
+  tf.twi = p->tn.twi;
+  return d;
+}
+
+// The persistent part of one run: reset the counters, one launch.
+static int run_persistent(fnt_rs_ragged_s* r, cudaStream_t st) {
+  if (!r->npersistent) return FNT_RS_OK;
+  if (cudaMemsetAsync(r->d_counters, 0, r->counter_bytes, st) != cudaSuccess)
+    return FNT_RS_E_CUDA;
+  if (launch_ragged(r->ra, r->grid, st) != 0) return FNT_RS_E_CUDA;
+  return cuda_ok(cudaGetLastError());
+}
 
 }  // namespace fntrs
 
@@ -70,6 +195,9 @@ void fnt_rs_ragged_destroy(fnt_rs_ragged r) {
   if (r->exec) cudaGraphExecDestroy(r->exec);
   if (r->graph) cudaGraphDestroy(r->graph);
   for (auto& g : r->groups) free_group(g);
+  cudaFree(r->d_groups);
+  cudaFree(r->d_items);
+  cudaFree(r->d_counters);
   for (void* w : r->ws) cudaFree(w);
   for (auto s : r->streams) cudaStreamDestroy(s);
   for (auto e : r->joins) cudaEventDestroy(e);
@@ -119,9 +247,65 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
         cudaSuccess)
       return fail(FNT_RS_E_CUDA);
   }
-  // plan classes -> streams, heaviest first onto the least-loaded stream
+  // groups of the persistent kernel: own build scratch, device records, work list
+  std::vector<int> pers;
+  for (int i = 0; i < (int)r->groups.size(); ++i) {
+    RaggedGroup& rg = r->groups[i];
+    rg.persistent = persistent_eligible(rg.plan);
+    if (!rg.persistent) continue;
+    pers.push_back(i);
+    if (rg.g.positions) {
+      const size_t n = rg.plan->n;
+      if (cudaMalloc(&rg.scratch, (n * rg.plan->lg_D + 6 * n) * 4) != cudaSuccess)
+        return fail(FNT_RS_E_CUDA);
+    }
+  }
+  if (!pers.empty()) {
+    auto cost = [&](int i) {
+      const double n = r->groups[i].plan->n;
+      return (double)r->groups[i].g.W * n * std::log2(n);
+    };
+    std::stable_sort(pers.begin(), pers.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<RaggedGroupDev> dg;
+    std::vector<RaggedItem> items;
+    for (int gi = 0; gi < (int)pers.size(); ++gi) {
+      dg.push_back(make_dev_group(r->groups[pers[gi]]));
+      for (int t = 0; t < dg.back().enc_tiles; ++t) items.push_back({RI_ENC, gi, t});
+    }
+    for (int gi = 0; gi < (int)pers.size(); ++gi)
+      if (dg[gi].has_plan)
+        for (int t = 0; t < dg[gi].plan.D; ++t) items.push_back({RI_PLAN, gi, t});
+    for (int gi = 0; gi < (int)pers.size(); ++gi) {
+      if (!dg[gi].has_plan) continue;
+      const int wt = ragged_wt_dec(dg[gi].L, dg[gi].blocked != 0);
+      const int tiles = (dg[gi].dec.W + wt - 1) / wt;
+      for (int t = 0; t < tiles; ++t) items.push_back({RI_DEC, gi, t});
+    }
+    const size_t G = dg.size();
+    r->counter_bytes = (1 + 2 * G) * sizeof(unsigned);
+    if (cudaMalloc(&r->d_groups, G * sizeof(RaggedGroupDev)) != cudaSuccess ||
+        cudaMalloc(&r->d_items, items.size() * sizeof(RaggedItem)) != cudaSuccess ||
+        cudaMalloc(&r->d_counters, r->counter_bytes) != cudaSuccess ||
+        cudaMemcpy(r->d_groups, dg.data(), G * sizeof(RaggedGroupDev), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(r->d_items, items.data(), items.size() * sizeof(RaggedItem),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(FNT_RS_E_CUDA);
+    r->ra.items = r->d_items;
+    r->ra.nitems = (int)items.size();
+    r->ra.groups = r->d_groups;
+    r->ra.next = r->d_counters;
+    r->ra.enc_done = r->d_counters + 1;
+    r->ra.plan_done = r->d_counters + 1 + G;
+    r->npersistent = (int)G;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->dev);
+    r->grid = std::max(1, sms);
+  }
+  // the other groups' plan classes -> streams, heaviest first onto the least-loaded stream
   std::map<fnt_rs_plan_s*, double> work;
   for (auto& rg : r->groups) {
+    if (rg.persistent) continue;
     const double n = rg.plan->n;
     work[rg.plan] += (double)rg.g.W * n * std::log2(n) * (rg.g.positions ? 4.0 : 1.0);
   }
@@ -140,6 +324,7 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
   r->ws.assign(S, nullptr);
   std::vector<size_t> wsb(S, 0);
   for (auto& rg : r->groups) {
+    if (rg.persistent) continue;
     rg.stream = assign[rg.plan];
     fnt_rs_plan_s* p = rg.plan;
     size_t need = ws_bytes(p, rg.g.W, enc_nbuf(p));
@@ -152,7 +337,12 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     if (wsb[s] && cudaMalloc(&r->ws[s], wsb[s]) != cudaSuccess) return fail(FNT_RS_E_CUDA);
   }
   // warm-up run (uncaptured): sets kernel attributes, fills table caches
+  {
+    int rc = run_persistent(r, st);
+    if (rc) return fail(rc);
+  }
   for (auto& rg : r->groups) {
+    if (rg.persistent) continue;
     const int rc = run_group(rg, r->ws[rg.stream], st);
     if (rc) return fail(rc);
   }
@@ -171,8 +361,9 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
   cudaEventRecord(r->fork, r->cap);
   for (uint32_t s = 0; s < S; ++s) cudaStreamWaitEvent(r->streams[s], r->fork, 0);
   for (auto& rg : r->groups) {
-    if (!rc) rc = run_group(rg, r->ws[rg.stream], r->streams[rg.stream]);
+    if (!rc && !rg.persistent) rc = run_group(rg, r->ws[rg.stream], r->streams[rg.stream]);
   }
+  if (!rc) rc = run_persistent(r, r->cap);
   for (uint32_t s = 0; s < S; ++s) {
     cudaEventRecord(r->joins[s], r->streams[s]);
     cudaStreamWaitEvent(r->cap, r->joins[s], 0);
@@ -216,8 +407,9 @@ int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream) {
 
 int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap) {
   if (!r || !info) return 0;
-  int vals[3] = {(int)r->groups.size(), (int)r->plans.size(), (int)r->streams.size()};
-  const int m = std::min(cap, 3);
+  int vals[5] = {(int)r->groups.size(), (int)r->plans.size(), (int)r->streams.size(),
+                 r->npersistent, r->ra.nitems};
+  const int m = std::min(cap, 5);
   for (int i = 0; i < m; ++i) info[i] = vals[i];
   return m;
 }

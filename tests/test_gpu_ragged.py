@@ -48,6 +48,7 @@ def test_ragged_graph_round_trip_and_oracle(pkg):
     try:
         info = pkg.fnt_rs_ragged_info(r)
         assert info["groups"] == 36
+        assert 0 < info["persistent_groups"] < 36  # tile-sized codes in the persistent kernel
         for g in groups:  # creation already ran the batch once; clear and rerun by graph
             g["enc"].zero_()
             g["out"].zero_()
@@ -89,5 +90,50 @@ def test_ragged_same_alone_and_in_mix(pkg):
             if g["positions"] is not None:
                 alone = plan.decode_slots(pkg.to_device(mix_enc[i]), g["positions"])
                 assert np.array_equal(pkg.to_host(alone), mix_out[i])
+    finally:
+        pkg.fnt_rs_ragged_destroy(r)
+
+
+def test_ragged_persistent_kernel_groups(pkg):
+    # only tile-sized codes (256 <= n <= 8192, every rate): the whole batch runs
+    # in the persistent kernel; 48 groups over 6 lengths and 4 rates means many
+    # groups share a plan, so their pattern builds run side by side in one launch
+    groups = _groups(pkg, seed=47, ngroups=48, log2n=(8, 13), log2w=(2, 8))
+    r = pkg.fnt_rs_ragged_create(groups, nstreams=4)
+    try:
+        info = pkg.fnt_rs_ragged_info(r)
+        assert info["persistent_groups"] == 48
+        assert info["persistent_items"] > 48
+        rng = np.random.default_rng(9)
+        first = None
+        for rep in range(3):  # the graph's counters start from zero on every run
+            for g in groups:
+                g["enc"].zero_()
+                g["out"].zero_()
+            pkg.fnt_rs_ragged_run(r)
+            torch.cuda.synchronize()
+            assert pkg.fnt_rs_ragged_status(r) == 0
+            got = [(pkg.to_host(g["enc"]), pkg.to_host(g["out"])) for g in groups]
+            if first is None:
+                first = got
+            for i, g in enumerate(groups):
+                assert np.array_equal(got[i][0], first[i][0]) and np.array_equal(got[i][1],
+                                                                                  first[i][1])
+                if g["positions"] is not None:
+                    assert np.array_equal(got[i][1], g["src_h"]), (g["n"], g["k"])
+        for i, g in enumerate(groups):
+            n = g["n"]
+            c = int(rng.integers(0, g["src_h"].shape[1]))
+            want = oracle.encode(np.ascontiguousarray(g["src_h"][:, [c]]), n)
+            assert np.array_equal(first[i][0][:, [c]], want), (n, g["k"])
+        # per-group plain launches give the same bits
+        for g in groups:
+            g["enc"].zero_()
+            g["out"].zero_()
+        pkg.fnt_rs_ragged_run_plain(r)
+        torch.cuda.synchronize()
+        for i, g in enumerate(groups):
+            assert np.array_equal(pkg.to_host(g["enc"]), first[i][0])
+            assert np.array_equal(pkg.to_host(g["out"]), first[i][1])
     finally:
         pkg.fnt_rs_ragged_destroy(r)
