@@ -20,6 +20,8 @@ template <> struct SchedFor<1024> { using type = Sched<1024, 32, 32>; };
 template <> struct SchedFor<2048> { using type = Sched<2048, 16, 16, 8>; };
 template <> struct SchedFor<4096> { using type = Sched<4096, 16, 16, 16>; };
 template <> struct SchedFor<8192> { using type = Sched<8192, 32, 16, 16>; };
+template <> struct SchedFor<16384> { using type = Sched<16384, 32, 32, 16>; };
+template <> struct SchedFor<32768> { using type = Sched<32768, 32, 32, 32>; };
 
 // Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
 template <class Tag, class F>
@@ -103,9 +105,12 @@ TileOps make_tile_ops() {
   ops.fnt_inv = &launch_tile<S, W1, NT, true, LoadRows32<W1>, StoreRows32<W1>>;
   ops.lossless = &launch_tile<S, W1, NT, true, LoadRows32<W1>, StoreFirstK16<W1>>;
   ops.decode = &launch_decode<S, W1, NT>;
-  ops.decode_split = &launch_decode_split<S, W2, NT>;
-  if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;
-  if constexpr (L >= 64) {
+  // two-buffer kernels need one codeword of two L-word buffers per CTA
+  if constexpr (W2 > 0) {
+    ops.decode_split = &launch_decode_split<S, W2, NT>;
+    if constexpr (S::NP >= 2) ops.poly_level = &launch_poly_level<S, W2, NT>;
+  }
+  if constexpr (L >= 64 && (Lay<S, 1>::WORDS + L) * 4 <= 227 * 1024) {
     ops.plan_fused = &launch_plan_fused<S, 512>;
   }
   return ops;

@@ -55,7 +55,8 @@ struct fnt_rs_plan_s {
   int C = 1;
   bool blocked = false;  // k > n/2
   fntrs::Tables tn;             // tables of length n (pow tables; schedule tables if n <= tile)
-  fntrs::Tables tl;             // tables of the local length (split only)
+  fntrs::Tables tl;             // tables of the local length (n > 8192)
+  int C_local = 1;              // n / kLocalL (n > 8192)
   fntrs::Tables tenc;           // schedule tables of the TMA encode's tile length
   uint32_t* twc = nullptr;  // TMA encode, class 1 of n = 2L: pass-1 twiddles times r_n^i2
   // log-domain pattern build: digits of g[d] = log_3(1 - r^d), b bits each
@@ -93,6 +94,10 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st,
 bool fused_plan_applies(const fnt_rs_plan_s* p);
 size_t pattern_scratch_words(uint32_t n, uint32_t k);
 int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
+// Encode of n > 8192 in two passes (radix-n/4096 cross pass, 4096-point
+// local transforms) through `work` of ws_bytes(p, W, enc_nbuf(p)) bytes.
+int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                       size_t ld_enc, size_t W, uint32_t* work, cudaStream_t st);
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
               size_t W, void* workspace, cudaStream_t st);
 // decode with explicit pattern tables (slots != 0: row z of recv is position z)

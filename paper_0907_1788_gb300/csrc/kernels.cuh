@@ -8,6 +8,18 @@
 
 namespace fntrs {
 
+// Loads of decode tables and received words: through the read-only cache
+// (CG = false) or through L2 only (CG = true, for data that other CTAs of the
+// same launch may have written, as in the ragged persistent kernel).
+template <bool CG, class T>
+__device__ __forceinline__ T ld_tab(const T* p) {
+  if constexpr (CG) {
+    return __ldcg(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Loaders: element i (0 <= i < L) of tile codeword c.
 // ---------------------------------------------------------------------------
@@ -69,10 +81,9 @@ struct LoadRows32 {
 // u[z] = v_i * c_i at z = z_i (the first k received positions), 0 elsewhere,
 // with c_i = -r^(-z_i) / A'(r^(z_i)) from the pattern table (weight 0 marks
 // an unused position).  Received values above 65536 are flagged once per
-// thread at the end of the kernel (see flush()).  Table and received words
-// are read through L2: in a ragged launch they may have been written by
-// other CTAs of the same kernel.
-template <int WT>
+// thread at the end of the kernel (see flush()).  With CG the table and the
+// received words are read through L2 (see ld_tab).
+template <int WT, bool CG = false>
 struct LoadRecv {
   const uint32_t* recv;
   size_t ld;
@@ -87,11 +98,11 @@ struct LoadRecv {
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) {
     const int col = col0 + c;
-    const uint2 e = __ldcg(pat + i);
+    const uint2 e = ld_tab<CG>(pat + i);
     uint32_t v = 0u;
     if (e.y != 0u && col < W) {
       const size_t row = slots ? (size_t)i : (size_t)e.x;
-      v = __ldcg(recv + row * ld + col);
+      v = CG ? __ldcg(recv + row * ld + col) : recv[row * ld + col];
     }
     bad |= v > 65536u ? 1u : 0u;
     return m_mul(v, e.y);
@@ -472,12 +483,12 @@ struct NopStore {
   __device__ __forceinline__ void operator()(int, int, uint32_t) const {}
 };
 
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, bool CG = false>
 __device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   using Y = Lay<S, WT>;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
+  LoadRecv<WT, CG> load = LoadRecv<WT, CG>::make(a, tx, 0);
   StoreOut16<WT> store = StoreOut16<WT>::make(a, tx, 0);
   const uint32_t* __restrict__ ahat = a.ahat;
   if constexpr (S::NP == 1) {
@@ -493,7 +504,7 @@ __device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
       bitrev_regs<R>(x);
       dft_reg<R, false>(x);
 #pragma unroll
-      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldcg(ahat + bitrev(q, B)));
+      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], ld_tab<CG>(ahat + bitrev(q, B)));
       bitrev_regs<R>(x);
       dft_reg<R, true>(x);
 #pragma unroll
@@ -548,7 +559,7 @@ __device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
         bitrev_regs<R>(x);
         dft_reg<R, false>(x);
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldcg(ahat + bitrev(q, B) * SP + i2));
+        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], ld_tab<CG>(ahat + bitrev(q, B) * SP + i2));
         bitrev_regs<R>(x);
         dft_reg<R, true>(x);
         twiddle_regs<R>(x, tw1i + i2 * R);
@@ -735,10 +746,10 @@ __global__ void __launch_bounds__(NT, 1)
 // ---------------------------------------------------------------------------
 
 // One codeword per thread, everything in registers (L <= 32).
-template <int L, int WT, int NT>
+template <int L, int WT, int NT, bool CG>
 __device__ __forceinline__ void decode_split_regs(const KArgs& a, int tx) {
   constexpr int B = ilog2(L), H = L / 2;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
+  LoadRecv<WT, CG> load = LoadRecv<WT, CG>::make(a, tx, 0);
   StoreOut16<WT> store = StoreOut16<WT>::make(a, tx, 0);
   for (int c = threadIdx.x; c < WT; c += NT) {
     uint32_t x[L], y[L];
@@ -757,7 +768,7 @@ __device__ __forceinline__ void decode_split_regs(const KArgs& a, int tx) {
 #pragma unroll
     for (int q = 0; q < L; ++q) {
       const int i = bitrev(q, B);
-      const uint32_t a0 = __ldcg(a.ahat + i), a1 = __ldcg(a.ahat2 + i);
+      const uint32_t a0 = ld_tab<CG>(a.ahat + i), a1 = ld_tab<CG>(a.ahat2 + i);
       const uint32_t s0 = m_to_p(x[q]);
       x[q] = m_mul(s0, a0);
       y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
@@ -779,13 +790,13 @@ __device__ __forceinline__ void decode_split_regs(const KArgs& a, int tx) {
   store.flush();
 }
 
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, bool CG>
 __device__ __forceinline__ void decode_split_smem(const KArgs& a, int tx) {
   using Y = Lay<S, WT>;
   extern __shared__ uint4 smem_raw[];
   uint32_t* X = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* Yb = X + Y::WORDS;
-  LoadRecv<WT> load = LoadRecv<WT>::make(a, tx, 0);
+  LoadRecv<WT, CG> load = LoadRecv<WT, CG>::make(a, tx, 0);
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
   const int k = a.k;
@@ -850,7 +861,7 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a, int tx) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int i = bitrev(q, B) * SP + i2;
-        const uint32_t a0 = __ldcg(a.ahat + i), a1 = __ldcg(a.ahat2 + i);
+        const uint32_t a0 = ld_tab<CG>(a.ahat + i), a1 = ld_tab<CG>(a.ahat2 + i);
         const uint32_t s0 = m_to_p(x[q]);
         x[q] = m_mul(s0, a0);
         y[q] = m_add(m_mul(y[q], a0), m_mul(s0, a1));
@@ -910,12 +921,12 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a, int tx) {
   if (bad > 65535u) atomicOr(a.status, ST_RANGE);
 }
 
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, bool CG = false>
 __device__ __forceinline__ void decode_split_body(const KArgs& a, int tx) {
   if constexpr (S::NP == 1) {
-    decode_split_regs<S::L, WT, NT>(a, tx);
+    decode_split_regs<S::L, WT, NT, CG>(a, tx);
   } else {
-    decode_split_smem<S, WT, NT>(a, tx);
+    decode_split_smem<S, WT, NT, CG>(a, tx);
   }
 }
 

@@ -71,37 +71,40 @@ __device__ __forceinline__ void lg_final_one(const LogFinal& f, int j, uint32_t 
   lg_store(f, j, row, x, f.ahat ? __ldg(f.exp3 + lg_rjk_index(f, j)) : 0u);
 }
 
-// All L positions by one CTA of NT threads, loads batched per thread.
+// All L positions by one CTA of NT threads, loads batched per thread (at
+// most 16 positions per thread per round).
 template <int L, int NT>
 __device__ __forceinline__ void lg_final_block(const LogFinal& f) {
-  constexpr int PJ = (L + NT - 1) / NT;
-  uint32_t row[PJ], x[PJ], r[PJ];
-#pragma unroll
-  for (int u = 0; u < PJ; ++u) {
-    const int j = (int)threadIdx.x + u * NT;
-    row[u] = j < L ? __ldcg(&f.pat[j].x) : 0xFFFFFFFFu;
-    x[u] = 0u;
-  }
-  // digit-major so that each round has PJ independent loads in flight
-  for (int t = 0; t < f.D; ++t) {
+  constexpr int PJ = (L + NT - 1) / NT < 16 ? (L + NT - 1) / NT : 16;
+  for (int base = 0; base < L; base += PJ * NT) {
+    uint32_t row[PJ], x[PJ], r[PJ];
 #pragma unroll
     for (int u = 0; u < PJ; ++u) {
-      const int j = (int)threadIdx.x + u * NT;
-      if (j < L) x[u] += __ldcg(f.conv + (size_t)j * f.D + t) << (f.b * t);
+      const int j = base + (int)threadIdx.x + u * NT;
+      row[u] = j < L ? __ldcg(&f.pat[j].x) : 0xFFFFFFFFu;
+      x[u] = 0u;
     }
-  }
+    // digit-major so that each round has PJ independent loads in flight
+    for (int t = 0; t < f.D; ++t) {
 #pragma unroll
-  for (int u = 0; u < PJ; ++u) {
-    const int j = (int)threadIdx.x + u * NT;
-    if (j < L) {
-      r[u] = f.ahat ? __ldg(f.exp3 + lg_rjk_index(f, j)) : 0u;
-      x[u] = __ldg(f.exp3 + lg_exp_index(f, j, row[u], x[u]));
+      for (int u = 0; u < PJ; ++u) {
+        const int j = base + (int)threadIdx.x + u * NT;
+        if (j < L) x[u] += __ldcg(f.conv + (size_t)j * f.D + t) << (f.b * t);
+      }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < PJ; ++u) {
-    const int j = (int)threadIdx.x + u * NT;
-    if (j < L) lg_store(f, j, row[u], x[u], r[u]);
+    for (int u = 0; u < PJ; ++u) {
+      const int j = base + (int)threadIdx.x + u * NT;
+      if (j < L) {
+        r[u] = f.ahat ? __ldg(f.exp3 + lg_rjk_index(f, j)) : 0u;
+        x[u] = __ldg(f.exp3 + lg_exp_index(f, j, row[u], x[u]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PJ; ++u) {
+      const int j = base + (int)threadIdx.x + u * NT;
+      if (j < L) lg_store(f, j, row[u], x[u], r[u]);
+    }
   }
 }
 

@@ -41,6 +41,7 @@ static void init_ops() {
     register_tile_ops_small();
     register_tile_ops_mid();
     register_tile_ops_big();
+    register_tile_ops_huge();
   });
 }
 
@@ -256,7 +257,7 @@ size_t split_chunk(uint32_t n, int nbuf) {
   return wc;
 }
 
-int enc_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+int enc_nbuf(const fnt_rs_plan_s* p) { return p->n > 8192 ? 1 : 0; }  // two-pass encode
 int dec_nbuf(const fnt_rs_plan_s* p) { return p->split ? (p->blocked ? 4 : 2) : 0; }
 int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
 
@@ -331,7 +332,7 @@ size_t pattern_scratch_words(uint32_t n, uint32_t k) {
   size_t K2 = 1;
   while (K2 < k) K2 <<= 1;
   const size_t lvl = 4 * (size_t)k + 4 * 64 + 2 * K2 + 64;
-  const size_t big = (K2 > (size_t)kTileMaxL / 2) ? 8 * (size_t)(2 * K2) + 8 * K2 : 0;
+  const size_t big = (K2 > (size_t)kTreeTileL / 2) ? 8 * (size_t)(2 * K2) + 8 * K2 : 0;
   const size_t tree = 2 * lvl + 9 * (size_t)n + big + 1024;
   // log route: ind, spec, aval, coef (n each), M2, E2 (2n each), P, conv, work (n*16 each)
   const size_t lg = 8 * (size_t)n + 3 * 16 * (size_t)n + 1024;
@@ -449,7 +450,7 @@ int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   while (nodes > 1) {
     const int L = 2 * d, npairs = (nodes + 1) / 2;
     uint32_t* dst = lv[cur ^ 1];
-    if (L <= kTileMaxL) {
+    if (L <= kTreeTileL) {
       Tables t;
       if ((rc = get_tables(L, &t))) return rc;
       KArgs a;
@@ -594,25 +595,34 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
   const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
   if (t != 1) return t;
-  if (!p->split) {
-    const TileOps& ops = tile_ops((int)p->n);
-    KArgs a;
-    a.in = src;
-    a.ld_in = ld_src;
-    a.out = enc;
-    a.ld_out = ld_enc;
-    a.W = (int)W;
-    a.n = (int)p->n;
-    a.k = (int)p->k;
+  KArgs a;
+  a.in = src;
+  a.ld_in = ld_src;
+  a.out = enc;
+  a.ld_out = ld_enc;
+  a.W = (int)W;
+  a.n = (int)p->n;
+  a.k = (int)p->k;
+  a.powf = p->tn.powf;
+  a.row_mul = p->uinv;
+  if (p->n <= 8192) {
     a.L = (int)p->n;
     a.C = 1;
     a.twf = p->tn.twf;
     a.twi = p->tn.twi;
-    a.powf = p->tn.powf;
-    a.row_mul = p->uinv;
-    ops.encode(a, 1, st);
+    tile_ops((int)p->n).encode(a, 1, st);
     return cuda_ok(cudaGetLastError());
   }
+  // longer codes: radix-C cross pass + 4096-point local transforms through the
+  // caller's workspace (measured faster than one CTA per 1-2 codewords, whose
+  // 4-8-byte row accesses waste most of each memory sector)
+  return do_encode_two_pass(p, src, ld_src, enc, ld_enc, W, static_cast<uint32_t*>(workspace),
+                            st);
+}
+
+int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                       size_t ld_enc, size_t W, uint32_t* workspace, cudaStream_t st) {
+  if (p->n <= 8192) return do_encode(p, src, ld_src, enc, ld_enc, W, nullptr, st);
   const size_t wc = split_chunk(p->n, 1);
   uint32_t* work = static_cast<uint32_t*>(workspace);
   for (size_t c0 = 0; c0 < W; c0 += wc) {
@@ -628,18 +638,18 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
     a.n = (int)p->n;
     a.k = (int)p->k;
     a.L = kLocalL;
-    a.C = p->C;
+    a.C = p->C_local;
     a.row_limit = (int)p->k;
     a.powf = p->tn.powf;
     a.powi = p->tn.powi;
     a.row_mul = p->uinv;
-    cross_launcher(p->C, false, CL_SRC16)(a, 1, st);
+    cross_launcher(p->C_local, false, CL_SRC16)(a, 1, st);
     KArgs b = a;
     b.in = work;
     b.ld_in = (size_t)w;
     b.twf = p->tl.twf;
     b.twi = p->tl.twi;
-    local_launcher(false, LM_ENC)(b, p->C, st);
+    local_launcher(false, LM_ENC)(b, p->C_local, st);
   }
   return cuda_ok(cudaGetLastError());
 }
@@ -649,7 +659,7 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
 // returns 1 if not applicable.
 static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                       size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
-  if (p->no_tma || p->split || p->blocked || p->n < 64) return 1;
+  if (p->no_tma || p->split || p->blocked || p->n < 64 || p->n > 8192) return 1;
   if ((reinterpret_cast<uintptr_t>(recv) % 16) != 0 || (ld_recv * 4) % 16 != 0) return 1;
   auto fn = tmap_encode_fn();
   if (!fn) return 1;
@@ -843,11 +853,14 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
   for (int it = 0; it < 5; ++it) ui = ui * (2u - u * ui);
   p->uinv = ui & (n - 1);
   p->ninv = hinv(n % FNT_RS_P);
-  p->split = n > (uint32_t)kTileMaxL;
+  // one CTA holds the transform unless the decode would need two buffers of a
+  // 32768-point codeword (k > n/2) or n exceeds the tile limit
+  p->split = n > (uint32_t)kTileMaxL || (n == (uint32_t)kTileMaxL && 2 * k > n);
   p->C = p->split ? (int)(n / kLocalL) : 1;
   p->blocked = k > n / 2;
+  p->C_local = n > 8192 ? (int)(n / kLocalL) : 1;
   int rc = get_tables((int)n, &p->tn);
-  if (!rc && p->split) rc = get_tables(kLocalL, &p->tl);
+  if (!rc && n > 8192) rc = get_tables(kLocalL, &p->tl);
   auto fail = [&](int code) {
     fnt_rs_plan_destroy(p);
     return code;

@@ -79,7 +79,7 @@ static void free_group(RaggedGroup& rg) {
 }
 
 static bool persistent_eligible(const fnt_rs_plan_s* p) {
-  return p->n >= (uint32_t)kRaggedMinL && p->n <= (uint32_t)kTileMaxL && p->u == 1 &&
+  return p->n >= (uint32_t)kRaggedMinL && p->n <= (uint32_t)kRaggedMaxL && p->u == 1 &&
          !p->plan_tree && fused_plan_applies(p);
 }
 

@@ -1,7 +1,7 @@
-// Work list of the ragged persistent kernel (k_ragged): every group with a
-// tile-sized code (256 <= n <= kTileMaxL) contributes encode tiles, pattern
-// digit builds (decode groups) and decode tiles; one launch of k_ragged runs
-// them all, each CTA taking work items in list order from an atomic counter.
+// Work list of the ragged persistent kernel (k_ragged): every group with
+// 256 <= n <= 8192 contributes encode tiles, pattern digit builds (decode
+// groups) and decode tiles; one launch of k_ragged runs them all, each CTA
+// taking work items in list order from an atomic counter.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,6 +42,7 @@ struct RaggedArgs {
 
 // Tile lengths the ragged kernel handles, all with 512 threads per CTA.
 constexpr int kRaggedMinL = 256;
+constexpr int kRaggedMaxL = 8192;
 constexpr int kRaggedNT = 512;
 
 // Dynamic shared memory of k_ragged (the largest body it runs).

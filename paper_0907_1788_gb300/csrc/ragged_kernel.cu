@@ -1,5 +1,5 @@
 // The ragged persistent kernel: one launch runs the encode tiles, pattern
-// builds and decode tiles of every group with 256 <= n <= kTileMaxL in a
+// builds and decode tiles of every group with 256 <= n <= 8192 in a
 // ragged batch.  CTAs stay resident and take work items in list order from an
 // atomic counter; the list puts all encode and pattern items before the
 // decode items, so a decode item only ever waits (boundedly) on items that
@@ -27,12 +27,12 @@ __device__ __noinline__ void rg_encode(const KArgs& a, int tx) {
 
 template <int L>
 __device__ __noinline__ void rg_decode(const KArgs& a, int tx) {
-  decode_body<RS<L>, wt_one(L), NT>(a, tx);
+  decode_body<RS<L>, wt_one(L), NT, true>(a, tx);
 }
 
 template <int L>
 __device__ __noinline__ void rg_decode_split(const KArgs& a, int tx) {
-  decode_split_body<RS<L>, wt_two(L), NT>(a, tx);
+  decode_split_body<RS<L>, wt_two(L), NT, true>(a, tx);
 }
 
 template <int L>

@@ -4,9 +4,12 @@
 
 namespace fntrs {
 
-// Largest transform held by one CTA; longer codes split n = C * kLocalL.
-constexpr int kTileMaxL = 8192;
+// Largest transform held by one CTA (u32 words, at most 128 KB of shared
+// memory per buffer); codes that do not fit split n = C * kLocalL.
+constexpr int kTileMaxL = 32768;
 constexpr int kLocalL = 4096;
+// Largest tile length of the product-tree route's pairwise products.
+constexpr int kTreeTileL = 8192;
 
 // radix factorisation of each tile length (each radix <= 32)
 inline void sched_radices(int L, int r[3]) {
@@ -20,6 +23,8 @@ inline void sched_radices(int L, int r[3]) {
     case 2048: r[0] = 16; r[1] = 16; r[2] = 8; break;
     case 4096: r[0] = 16; r[1] = 16; r[2] = 16; break;
     case 8192: r[0] = 32; r[1] = 16; r[2] = 16; break;
+    case 16384: r[0] = 32; r[1] = 32; r[2] = 16; break;
+    case 32768: r[0] = 32; r[1] = 32; r[2] = 32; break;
     default: break;  // L <= 32: one pass
   }
 }
@@ -51,6 +56,7 @@ const TileOps& tile_ops(int L);
 void register_tile_ops_small();
 void register_tile_ops_mid();
 void register_tile_ops_big();
+void register_tile_ops_huge();
 
 // TMA-staged encode for tile length L (C = 1) or n = 2L (C = 2).
 // Returns -1 if the configuration has no instantiation.

@@ -124,7 +124,7 @@ def test_fnt_matches_dft_definition(pkg, n, W):
     assert np.array_equal(inv, oracle.dft(xm, inverse=True))
 
 
-@pytest.mark.parametrize("n,W", [(16384, 5), (65536, 4)])
+@pytest.mark.parametrize("n,W", [(16384, 5), (32768, 3), (65536, 4)])
 def test_fnt_split_roundtrip_and_encode_consistency(pkg, n, W):
     rng = np.random.default_rng(n)
     x = rng.integers(0, P, size=(n, W), dtype=np.uint32)
@@ -164,7 +164,7 @@ def test_decode_random_received_matches_oracle(pkg, n, k, W):
 
 
 @pytest.mark.parametrize("n,k,W", [(16384, 8192, 8), (16384, 12000, 5), (65536, 32768, 3),
-                                   (32768, 30000, 3)])
+                                   (32768, 30000, 3), (32768, 16384, 4), (32768, 10000, 3)])
 def test_decode_split_sizes_sampled(pkg, n, k, W):
     seed = n + k
     rng = np.random.default_rng(seed)
@@ -178,7 +178,8 @@ def test_decode_split_sizes_sampled(pkg, n, k, W):
 
 
 @pytest.mark.parametrize("n,k,W", [(16384, 8192, 64), (65536, 32768, 16), (32768, 28672, 8),
-                                   (8192, 7168, 32), (256, 224, 200)])
+                                   (32768, 16384, 6), (16384, 12000, 16), (8192, 7168, 32),
+                                   (256, 224, 200)])
 def test_roundtrip_every_codeword(pkg, n, k, W):
     src = synth.source(n * 3 + 1, k, W)
     plan = pkg.Plan(n, k)
@@ -192,7 +193,8 @@ def test_roundtrip_every_codeword(pkg, n, k, W):
 
 @pytest.mark.parametrize("n,k,W", [(64, 32, 36), (256, 100, 68), (1024, 512, 40),
                                    (2048, 1024, 20), (4096, 2048, 24), (8192, 4096, 12),
-                                   (8192, 4096, 2048), (8192, 6000, 8), (16384, 8192, 8)])
+                                   (8192, 4096, 2048), (8192, 6000, 8), (16384, 8192, 8),
+                                   (16384, 12000, 4), (32768, 16000, 4)])
 @pytest.mark.parametrize("route", ["log", "tree"])
 def test_decode_paths_and_plan_routes(pkg, n, k, W, route, monkeypatch):
     # plan tables by the log-domain correlation (default) or the product tree;
