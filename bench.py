@@ -363,6 +363,13 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     plan = pkg.Plan(n, k, device=dev)
 
+    # schedules: time every one that can run this workload and keep the fastest
+    tuned = {}
+    for name, op in (("encode", pkg.OP_ENCODE), ("decode", pkg.OP_DECODE)):
+        res = plan.autotune(W, op, stream)
+        tuned[name] = {"timed_us": {pkg.SCHED_NAMES[s_]: round(us, 2) for s_, us in res},
+                       "chosen": pkg.SCHED_NAMES[plan.schedule(op)]}
+
     src = pkg.to_device(cfg.source(), dev)
     enc = torch.empty((n, W), dtype=torch.int32, device=dev)
     out = torch.empty((k, W), dtype=torch.int16, device=dev)
@@ -507,6 +514,7 @@ def run_gpu(args):
                    "step": "(decode plan -> decode of k received packets) || encode, two streams",
                    "l2": "flushed between steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
+        "autotune": tuned,
         "breakdown_ms": {"encode": enc_ms, "plan": pat_ms, "decode": dec_ms,
                          "serial_step": ms_serial},
         "encode_gbs": src_bytes / (enc_ms * 1e-3) / 1e9,

@@ -106,6 +106,55 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
                   size_t ld_enc, size_t W, void* workspace, void* stream);
 
 /*
+ * Schedules: how an encode or a decode is laid out on the GPU.  Every
+ * schedule computes the same words (the arithmetic is exact); they differ in
+ * staging and in how the length-n transform is split over CTAs and passes:
+ *   FNT_RS_SCHED_TMA    one CTA per tile of codewords, rows staged in shared
+ *                       memory by TMA (n <= 8192; decode also k <= n/2),
+ *   FNT_RS_SCHED_TILE   one CTA per tile, rows loaded directly (n <= 32768;
+ *                       decode: n <= 16384, or n = 32768 with k <= n/2),
+ *   FNT_RS_SCHED_SPLIT  radix-(n/4096) cross passes and 4096-point local
+ *                       passes through the workspace (encode n > 8192,
+ *                       decode n >= 16384).
+ * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else TILE
+ * (encode up to n = 8192; decode wherever one CTA holds the codeword), else
+ * SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
+ */
+enum fnt_rs_sched {
+  FNT_RS_SCHED_AUTO = 0,
+  FNT_RS_SCHED_TMA = 1,
+  FNT_RS_SCHED_TILE = 2,
+  FNT_RS_SCHED_SPLIT = 3
+};
+
+typedef struct fnt_rs_tune_result_s {
+  int sched; /* enum fnt_rs_sched */
+  float us;  /* median time of one call */
+} fnt_rs_tune_result;
+
+/* Forces the schedule of `op` (FNT_RS_OP_ENCODE or FNT_RS_OP_DECODE);
+ * FNT_RS_E_ARG if it cannot run this plan.  FNT_RS_SCHED_AUTO restores the
+ * default choice. */
+int fnt_rs_set_schedule(fnt_rs_plan plan, int op, int sched);
+/* The schedule `op` runs with now (never FNT_RS_SCHED_AUTO), or a negative error. */
+int fnt_rs_get_schedule(fnt_rs_plan plan, int op);
+
+/*
+ * Autotuner.  Runs every schedule of `op` that can run this plan on W
+ * codewords of zeroed data (at most 2^29 bytes of encoded words: a larger W
+ * is timed on fewer columns, a multiple of 8) in device buffers it allocates
+ * and frees itself, times each with CUDA events on `stream` (median of 5
+ * calls after 2 warm-up calls; the time of an integer transform does not
+ * depend on the data), keeps the fastest for the plan and writes up to `cap`
+ * {schedule, microseconds} entries to `out`.  A decode tune builds a pattern
+ * of its own in the plan's pattern cache (which may evict a cached pattern).
+ * Synchronises `stream`.  Returns the number of schedules timed, or a
+ * negative error (the plan's previous choice is then kept).
+ */
+int fnt_rs_autotune(fnt_rs_plan plan, size_t W, int op, fnt_rs_tune_result* out, int cap,
+                    void* stream);
+
+/*
  * Per-pattern preparation, steps 1-3 of the interpolation (Sec. II.B):
  * from the first k of `positions` (host array, npos >= k entries, distinct,
  * each < n) build on the device A(x) = prod (x - r^z_i), the weights
@@ -223,7 +272,9 @@ int fnt_rs_status(fnt_rs_plan plan, void* stream);
  * 256 <= n <= 8192 runs inside one launch of a persistent kernel (its CTAs
  * take the groups' encode tiles, pattern builds and decode tiles from one
  * work list); the other groups keep per-group launches spread over up to
- * `nstreams` streams.  Groups must not share output buffers.
+ * `nstreams` streams, their plans' schedules picked by fnt_rs_autotune on the
+ * widest group of each plan (environment FNTRS_AUTOTUNE=0 keeps the default
+ * schedules).  Groups must not share output buffers.
  */
 typedef struct fnt_rs_group_s {
   uint32_t n, k;
@@ -248,8 +299,9 @@ int fnt_rs_ragged_run(fnt_rs_ragged r, void* stream);
 int fnt_rs_ragged_run_plain(fnt_rs_ragged r, void* stream);
 /* ORs the status words of the batch's plans (synchronises `stream`). */
 int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream);
-/* {groups, plans, streams, groups in the persistent kernel, its work items};
- * returns the number of ints written (at most cap). */
+/* {groups, plans, streams, groups in the persistent kernel, its work items,
+ * plans whose schedules were autotuned}; returns the number of ints written
+ * (at most cap). */
 int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap);
 void fnt_rs_ragged_destroy(fnt_rs_ragged r);
 

@@ -23,6 +23,8 @@ from ._lib import FntRsError, Group, LIB_PATH, Request, load  # noqa: F401
 
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
+SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT = 0, 1, 2, 3
+SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split"}
 
 E_RANGE = -7
 E_TIMEOUT = -8
@@ -196,10 +198,10 @@ def fnt_rs_ragged_status(r, stream=None) -> int:
 
 
 def fnt_rs_ragged_info(r) -> dict:
-    buf = (ctypes.c_int * 5)()
-    m = load().fnt_rs_ragged_info(r, buf, 5)
-    return dict(zip(["groups", "plans", "streams", "persistent_groups", "persistent_items"],
-                    [int(buf[i]) for i in range(m)]))
+    buf = (ctypes.c_int * 6)()
+    m = load().fnt_rs_ragged_info(r, buf, 6)
+    return dict(zip(["groups", "plans", "streams", "persistent_groups", "persistent_items",
+                     "tuned_plans"], [int(buf[i]) for i in range(m)]))
 
 
 def fnt_rs_ragged_destroy(r):
@@ -302,6 +304,28 @@ def fnt_rs_baseline_replay(reqs, arrivals, stream=None):
     return lat, wall.value
 
 
+def fnt_rs_set_schedule(plan, op: int, sched: int) -> None:
+    _check(load().fnt_rs_set_schedule(plan, op, sched), "fnt_rs_set_schedule")
+
+
+def fnt_rs_get_schedule(plan, op: int) -> int:
+    rc = int(load().fnt_rs_get_schedule(plan, op))
+    if rc < 0:
+        _check(rc, "fnt_rs_get_schedule")
+    return rc
+
+
+def fnt_rs_autotune(plan, W: int, op: int, stream=None) -> list:
+    """Times every schedule of `op` for W codewords; returns [(sched, us)], keeps the fastest."""
+    from ._lib import TuneResult
+
+    buf = (TuneResult * 4)()
+    rc = int(load().fnt_rs_autotune(plan, W, op, buf, 4, _stream(stream)))
+    if rc < 0:
+        _check(rc, "fnt_rs_autotune")
+    return [(int(buf[i].sched), float(buf[i].us)) for i in range(rc)]
+
+
 def fnt_rs_status(plan, stream=None) -> int:
     return int(load().fnt_rs_status(plan, _stream(stream)))
 
@@ -393,6 +417,15 @@ class Plan:
 
     def status(self, stream=None) -> int:
         return fnt_rs_status(self.handle, stream)
+
+    def autotune(self, W: int, op: int, stream=None) -> list:
+        return fnt_rs_autotune(self.handle, W, op, stream)
+
+    def schedule(self, op: int) -> int:
+        return fnt_rs_get_schedule(self.handle, op)
+
+    def set_schedule(self, op: int, sched: int) -> None:
+        fnt_rs_set_schedule(self.handle, op, sched)
 
     def info(self) -> dict:
         return fnt_rs_plan_info(self.handle)

@@ -56,6 +56,9 @@ def load(build_if_missing: bool = False):
             "fnt_rs_encode_host": (i32, [vp, vp, vp, sz, vp, vp]),
             "fnt_rs_encode_noalloc": (i32, [vp, vp, sz, vp, sz, sz, vp]),
             "fnt_rs_decode_host": (i32, [vp, vp, vp, u32, vp, sz, vp, vp]),
+            "fnt_rs_set_schedule": (i32, [vp, i32, i32]),
+            "fnt_rs_get_schedule": (i32, [vp, i32]),
+            "fnt_rs_autotune": (i32, [vp, sz, i32, vp, i32, vp]),
             "fnt_rs_status": (i32, [vp, vp]),
             "fnt_rs_server_create": (i32, [ctypes.POINTER(vp), sz, u32, i32]),
             "fnt_rs_server_preplan": (i32, [vp, u32, u32]),
@@ -94,6 +97,12 @@ class Group(ctypes.Structure):
                 ("enc", ctypes.c_void_p), ("ld_enc", ctypes.c_size_t),
                 ("positions", ctypes.c_void_p), ("npos", ctypes.c_uint32),
                 ("out", ctypes.c_void_p), ("ld_out", ctypes.c_size_t)]
+
+
+class TuneResult(ctypes.Structure):
+    """fnt_rs_tune_result of include/fnt_rs.h."""
+
+    _fields_ = [("sched", ctypes.c_int), ("us", ctypes.c_float)]
 
 
 class Request(ctypes.Structure):

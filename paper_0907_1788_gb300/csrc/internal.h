@@ -66,6 +66,7 @@ struct fnt_rs_plan_s {
   uint32_t* exp3 = nullptr;  // shared table
   int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
   bool no_tma = false;
+  int sched_enc = 0, sched_dec = 0;  // fnt_rs_sched of encode / decode (0: automatic)
   int sms = 1;
   int* status = nullptr;
   uint32_t* pscratch = nullptr;
@@ -79,8 +80,14 @@ namespace fntrs {
 
 int cuda_ok(cudaError_t e);
 size_t split_chunk(uint32_t n, int nbuf);
+// workspace buffers of the schedule in use / the most any candidate schedule needs
 int enc_nbuf(const fnt_rs_plan_s* p);
 int dec_nbuf(const fnt_rs_plan_s* p);
+int enc_nbuf_max(const fnt_rs_plan_s* p);
+int dec_nbuf_max(const fnt_rs_plan_s* p);
+// schedules (fnt_rs_sched) an op can run with, and the one it runs with now
+bool sched_available(const fnt_rs_plan_s* p, int op, int sched);
+int sched_effective(const fnt_rs_plan_s* p, int op);
 int fnt_nbuf(const fnt_rs_plan_s* p);
 size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf);
 int get_tables(int L, Tables* out);

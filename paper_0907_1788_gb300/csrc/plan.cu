@@ -257,8 +257,50 @@ size_t split_chunk(uint32_t n, int nbuf) {
   return wc;
 }
 
-int enc_nbuf(const fnt_rs_plan_s* p) { return p->n > 8192 ? 1 : 0; }  // two-pass encode
-int dec_nbuf(const fnt_rs_plan_s* p) { return p->split ? (p->blocked ? 4 : 2) : 0; }
+// Schedules.  Encode: TMA-staged tile (n <= 8192 when the TMA shape exists),
+// one-CTA tile (n <= 32768), two-pass split (n > 8192).  Decode: TMA-staged
+// tile (64 <= n <= 8192, k <= n/2), one-CTA tile (n <= 16384, or n = 32768
+// with k <= n/2), split passes (n >= 16384).  All give the same words.
+bool sched_available(const fnt_rs_plan_s* p, int op, int s) {
+  const uint32_t n = p->n;
+  if (op == FNT_RS_OP_ENCODE) {
+    switch (s) {
+      case FNT_RS_SCHED_TMA: return p->enc_L != 0 && p->u == 1 && !p->no_tma;
+      case FNT_RS_SCHED_TILE: return n <= (uint32_t)kTileMaxL;
+      case FNT_RS_SCHED_SPLIT: return n > 8192;
+      default: return false;
+    }
+  }
+  if (op == FNT_RS_OP_DECODE) {
+    switch (s) {
+      case FNT_RS_SCHED_TMA: return n >= 64 && n <= 8192 && !p->blocked && !p->no_tma;
+      case FNT_RS_SCHED_TILE: return !p->split;
+      case FNT_RS_SCHED_SPLIT: return n >= 16384;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+int sched_effective(const fnt_rs_plan_s* p, int op) {
+  const int chosen = op == FNT_RS_OP_ENCODE ? p->sched_enc : p->sched_dec;
+  if (chosen) return chosen;
+  if (op == FNT_RS_OP_ENCODE) {
+    if (sched_available(p, op, FNT_RS_SCHED_TMA)) return FNT_RS_SCHED_TMA;
+    return p->n <= 8192 ? FNT_RS_SCHED_TILE : FNT_RS_SCHED_SPLIT;
+  }
+  if (sched_available(p, op, FNT_RS_SCHED_TMA)) return FNT_RS_SCHED_TMA;
+  return p->split ? FNT_RS_SCHED_SPLIT : FNT_RS_SCHED_TILE;
+}
+
+int enc_nbuf(const fnt_rs_plan_s* p) {
+  return sched_effective(p, FNT_RS_OP_ENCODE) == FNT_RS_SCHED_SPLIT ? 1 : 0;
+}
+int dec_nbuf(const fnt_rs_plan_s* p) {
+  return sched_effective(p, FNT_RS_OP_DECODE) == FNT_RS_SCHED_SPLIT ? (p->blocked ? 4 : 2) : 0;
+}
+int enc_nbuf_max(const fnt_rs_plan_s* p) { return p->n > 8192 ? 1 : 0; }
+int dec_nbuf_max(const fnt_rs_plan_s* p) { return p->n >= 16384 ? (p->blocked ? 4 : 2) : 0; }
 int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
 
 size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf) {
@@ -593,8 +635,14 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
 
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
-  const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
-  if (t != 1) return t;
+  const int sched = sched_effective(p, FNT_RS_OP_ENCODE);
+  if (sched == FNT_RS_SCHED_TMA) {
+    const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
+    if (t != 1) return t;  // else (unaligned pointers) the one-CTA tile below
+  }
+  if (sched == FNT_RS_SCHED_SPLIT)
+    return do_encode_two_pass(p, src, ld_src, enc, ld_enc, W, static_cast<uint32_t*>(workspace),
+                              st);
   KArgs a;
   a.in = src;
   a.ld_in = ld_src;
@@ -605,19 +653,12 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
   a.k = (int)p->k;
   a.powf = p->tn.powf;
   a.row_mul = p->uinv;
-  if (p->n <= 8192) {
-    a.L = (int)p->n;
-    a.C = 1;
-    a.twf = p->tn.twf;
-    a.twi = p->tn.twi;
-    tile_ops((int)p->n).encode(a, 1, st);
-    return cuda_ok(cudaGetLastError());
-  }
-  // longer codes: radix-C cross pass + 4096-point local transforms through the
-  // caller's workspace (measured faster than one CTA per 1-2 codewords, whose
-  // 4-8-byte row accesses waste most of each memory sector)
-  return do_encode_two_pass(p, src, ld_src, enc, ld_enc, W, static_cast<uint32_t*>(workspace),
-                            st);
+  a.L = (int)p->n;
+  a.C = 1;
+  a.twf = p->tn.twf;
+  a.twi = p->tn.twi;
+  tile_ops((int)p->n).encode(a, 1, st);
+  return cuda_ok(cudaGetLastError());
 }
 
 int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
@@ -702,9 +743,10 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
 int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
                      cudaStream_t st, int slots) {
-  if (!slots) {
+  const int sched = sched_effective(p, FNT_RS_OP_DECODE);
+  if (!slots && sched == FNT_RS_SCHED_TMA) {
     const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st);
-    if (t != 1) return t;
+    if (t != 1) return t;  // else (unaligned rows) the one-CTA tile below
   }
   KArgs a;
   a.slots = slots;
@@ -719,7 +761,7 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
   a.ahat = sl.ahat;
   a.ahat2 = sl.ahat2;
   a.status = p->status;
-  if (!p->split) {
+  if (sched != FNT_RS_SCHED_SPLIT) {
     const TileOps& ops = tile_ops((int)p->n);
     a.W = (int)W;
     a.L = (int)p->n;
@@ -745,7 +787,7 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
     c.out = out + c0;
     c.W = w;
     c.L = kLocalL;
-    c.C = p->C;
+    c.C = p->C_local;
     c.ld_work = (size_t)w;
     c.powf = p->tn.powf;
     c.powi = p->tn.powi;
@@ -757,7 +799,7 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
       x.ld_in = ld_in;
       x.row_limit = row_limit;
       x.out2 = A;
-      cross_launcher(p->C, inv, lm)(x, 1, st);
+      cross_launcher(p->C_local, inv, lm)(x, 1, st);
     };
     auto local = [&](bool inv, int mode, void* o2, void* o3, int out_limit, const void* in2) {
       KArgs x = c;
@@ -767,7 +809,7 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
       x.out3 = o3;
       x.in2 = in2;
       x.out_limit = out_limit;
-      local_launcher(inv, mode)(x, p->C, st);
+      local_launcher(inv, mode)(x, p->C_local, st);
     };
     if (!p->blocked) {
       cross(true, CL_RECV, recv + c0, ld_recv, (int)p->n);
@@ -957,16 +999,16 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
 size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
   if (!p) return 0;
   switch (op) {
-    case FNT_RS_OP_ENCODE: return ws_bytes(p, W, enc_nbuf(p));
-    case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf(p));
+    case FNT_RS_OP_ENCODE: return ws_bytes(p, W, enc_nbuf_max(p));
+    case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf_max(p));
     case FNT_RS_OP_FNT: return ws_bytes(p, W, fnt_nbuf(p));
     case FNT_RS_OP_ENCODE_HOST: {
       const size_t stage = ((size_t)p->k * W * 2 + 255) / 256 * 256 + (size_t)p->n * W * 4;
-      return stage + ws_bytes(p, W, enc_nbuf(p));
+      return stage + ws_bytes(p, W, enc_nbuf_max(p));
     }
     case FNT_RS_OP_DECODE_HOST: {
       const size_t stage = ((size_t)p->k * W * 4 + 255) / 256 * 256 + ((size_t)p->k * W * 2 + 255) / 256 * 256;
-      return stage + ws_bytes(p, W, dec_nbuf(p));
+      return stage + ws_bytes(p, W, dec_nbuf_max(p));
     }
     default: return 0;
   }
@@ -1124,6 +1166,94 @@ int fnt_rs_decode_host(fnt_rs_plan p, const uint32_t* h_recv, const uint32_t* po
   if ((rc = cuda_ok(cudaMemcpyAsync(h_out, d_out, (size_t)p->k * W * 2, cudaMemcpyDeviceToHost, st))))
     return rc;
   return cuda_ok(cudaStreamSynchronize(st));
+}
+
+int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
+  if (!p || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
+  if (sched != FNT_RS_SCHED_AUTO && !sched_available(p, op, sched)) return FNT_RS_E_ARG;
+  (op == FNT_RS_OP_ENCODE ? p->sched_enc : p->sched_dec) = sched;
+  return FNT_RS_OK;
+}
+
+int fnt_rs_get_schedule(fnt_rs_plan p, int op) {
+  if (!p || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
+  return sched_effective(p, op);
+}
+
+int fnt_rs_autotune(fnt_rs_plan p, size_t W, int op, fnt_rs_tune_result* out, int cap,
+                    void* stream) {
+  if (!p || W == 0 || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
+  std::vector<int> cand;
+  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT})
+    if (sched_available(p, op, s)) cand.push_back(s);
+  if (cand.empty()) return FNT_RS_E_ARG;
+  cudaStream_t st = S(stream);
+  const size_t n = p->n, k = p->k;
+  size_t w = std::min(W, std::max<size_t>(8, ((size_t)1 << 29) / (n * 4)));
+  if (w >= 8) w = w / 8 * 8;
+  const bool enc_op = op == FNT_RS_OP_ENCODE;
+  const size_t wsb = ws_bytes(p, w, enc_op ? enc_nbuf_max(p) : dec_nbuf_max(p));
+  uint16_t* src = nullptr;
+  uint32_t* enc = nullptr;
+  uint16_t* dout = nullptr;
+  void* ws = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int* saved = enc_op ? &p->sched_enc : &p->sched_dec;
+  const int keep = *saved;
+  std::vector<fnt_rs_tune_result> res;
+  int rc = FNT_RS_OK;
+  if (cudaMalloc(&src, k * w * 2) != cudaSuccess || cudaMalloc(&enc, n * w * 4) != cudaSuccess ||
+      cudaMalloc(&dout, k * w * 2) != cudaSuccess ||
+      (wsb && cudaMalloc(&ws, wsb) != cudaSuccess) ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemsetAsync(src, 0, k * w * 2, st) != cudaSuccess ||
+      cudaMemsetAsync(enc, 0, n * w * 4, st) != cudaSuccess)
+    rc = FNT_RS_E_CUDA;
+  if (!rc && !enc_op) {
+    // k distinct positions z_i = (a i + b) mod n (a odd: a bijection of Z/n)
+    std::vector<uint32_t> pos(k);
+    for (size_t i = 0; i < k; ++i) pos[i] = (uint32_t)((0x9E3779B1u * i + 12345u) & (n - 1));
+    rc = prepare(p, pos.data(), (uint32_t)k, st);
+  }
+  for (size_t ci = 0; !rc && ci < cand.size(); ++ci) {
+    *saved = cand[ci];
+    auto run = [&]() {
+      return enc_op ? do_encode(p, src, w, enc, w, w, ws, st)
+                    : do_decode_tables(p, p->slots[p->current], enc, w, dout, w, w, ws, st, 0);
+    };
+    float t[5];
+    for (int it = 0; it < 7 && !rc; ++it) {
+      if (it >= 2 && cudaEventRecord(e0, st) != cudaSuccess) rc = FNT_RS_E_CUDA;
+      if (!rc) rc = run();
+      if (!rc && it >= 2) {
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t[it - 2], e0, e1) != cudaSuccess)
+          rc = FNT_RS_E_CUDA;
+      }
+    }
+    if (!rc) {
+      std::sort(t, t + 5);
+      res.push_back({cand[ci], t[2] * 1000.0f});
+    }
+  }
+  if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = FNT_RS_E_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(src);
+  cudaFree(enc);
+  cudaFree(dout);
+  cudaFree(ws);
+  if (rc) {
+    *saved = keep;
+    return rc;
+  }
+  auto best = std::min_element(res.begin(), res.end(), [](const fnt_rs_tune_result& a,
+                                                          const fnt_rs_tune_result& b) {
+    return a.us < b.us;
+  });
+  *saved = best->sched;
+  for (int i = 0; i < cap && i < (int)res.size(); ++i) out[i] = res[i];
+  return (int)res.size();
 }
 
 int fnt_rs_status(fnt_rs_plan p, void* stream) {

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -58,6 +59,7 @@ struct fnt_rs_ragged_s {
   size_t counter_bytes = 0;
   int grid = 0;
   int npersistent = 0;
+  int tuned = 0;  // plans whose schedules the autotuner picked
 };
 
 namespace fntrs {
@@ -302,6 +304,27 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->dev);
     r->grid = std::max(1, sms);
   }
+  // schedules of the per-group launches: tune each such plan on its widest group
+  {
+    const char* e = std::getenv("FNTRS_AUTOTUNE");
+    if (!(e && e[0] == '0')) {
+      std::map<fnt_rs_plan_s*, std::pair<size_t, bool>> widest;  // W, any decode
+      for (auto& rg : r->groups) {
+        if (rg.persistent) continue;
+        auto& w = widest[rg.plan];
+        w.first = std::max(w.first, rg.g.W);
+        w.second = w.second || rg.g.positions != nullptr;
+      }
+      for (auto& kv : widest) {
+        fnt_rs_tune_result res[4];
+        int rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_ENCODE, res, 4, stream);
+        if (rc >= 0 && kv.second.second)
+          rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_DECODE, res, 4, stream);
+        if (rc < 0) return fail(rc);
+        ++r->tuned;
+      }
+    }
+  }
   // the other groups' plan classes -> streams, heaviest first onto the least-loaded stream
   std::map<fnt_rs_plan_s*, double> work;
   for (auto& rg : r->groups) {
@@ -327,8 +350,8 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     if (rg.persistent) continue;
     rg.stream = assign[rg.plan];
     fnt_rs_plan_s* p = rg.plan;
-    size_t need = ws_bytes(p, rg.g.W, enc_nbuf(p));
-    if (rg.g.positions) need = std::max(need, ws_bytes(p, rg.g.W, dec_nbuf(p)));
+    size_t need = ws_bytes(p, rg.g.W, enc_nbuf_max(p));
+    if (rg.g.positions) need = std::max(need, ws_bytes(p, rg.g.W, dec_nbuf_max(p)));
     wsb[rg.stream] = std::max(wsb[rg.stream], need);
   }
   for (uint32_t s = 0; s < S; ++s) {
@@ -407,9 +430,9 @@ int fnt_rs_ragged_status(fnt_rs_ragged r, void* stream) {
 
 int fnt_rs_ragged_info(fnt_rs_ragged r, int* info, int cap) {
   if (!r || !info) return 0;
-  int vals[5] = {(int)r->groups.size(), (int)r->plans.size(), (int)r->streams.size(),
-                 r->npersistent, r->ra.nitems};
-  const int m = std::min(cap, 5);
+  int vals[6] = {(int)r->groups.size(), (int)r->plans.size(), (int)r->streams.size(),
+                 r->npersistent, r->ra.nitems, r->tuned};
+  const int m = std::min(cap, 6);
   for (int i = 0; i < m; ++i) info[i] = vals[i];
   return m;
 }

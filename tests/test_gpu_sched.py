@@ -94,3 +94,59 @@ def test_encode_concurrent_with_decode(pkg, decode_on_main):
         assert np.array_equal(pkg.to_host(d_out), src_b), rep
         assert np.array_equal(pkg.to_host(d_enc), serial_enc), rep
     assert plan.status() == 0
+
+
+# ------------------------------------------------------------------ schedules
+@pytest.mark.parametrize("n,k,W", [(1024, 512, 256), (8192, 4096, 64), (8192, 6000, 32),
+                                   (16384, 8192, 24), (16384, 12000, 8), (32768, 16384, 8)])
+def test_every_schedule_gives_the_same_words(pkg, n, k, W):
+    seed = 17 * n + k
+    src = synth.source(seed, k, W)
+    pos = synth.received_positions(n, synth.erased_uniform(seed + 1, n, k))
+    v = synth.received_uniform(seed + 2, k, W)
+    plan = pkg.Plan(n, k)
+    encs, decs = {}, {}
+    for s in (pkg.SCHED_TMA, pkg.SCHED_TILE, pkg.SCHED_SPLIT):
+        try:
+            plan.set_schedule(pkg.OP_ENCODE, s)
+        except pkg.FntRsError:
+            pass
+        else:
+            assert plan.schedule(pkg.OP_ENCODE) == s
+            encs[s] = pkg.to_host(plan.encode(pkg.to_device(src)))
+        try:
+            plan.set_schedule(pkg.OP_DECODE, s)
+        except pkg.FntRsError:
+            pass
+        else:
+            decs[s] = pkg.to_host(plan.decode(pkg.to_device(v), pos))
+    plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_AUTO)
+    plan.set_schedule(pkg.OP_DECODE, pkg.SCHED_AUTO)
+    assert len(encs) >= 1 and len(decs) >= 1
+    if n > 8192:
+        assert len(encs) == 2 and len(decs) == 2  # one-CTA tile and split both run
+    first_e, first_d = next(iter(encs.values())), next(iter(decs.values()))
+    for e in encs.values():
+        assert np.array_equal(e, first_e)
+    for d in decs.values():
+        assert np.array_equal(d, first_d)
+    cols = [0, W - 1]
+    assert np.array_equal(first_e[:, cols], oracle.encode(np.ascontiguousarray(src[:, cols]), n))
+    want, _ = oracle.decode(np.ascontiguousarray(v[:, cols]), pos, n, k)
+    assert np.array_equal(first_d[:, cols], want)
+
+
+def test_autotune_keeps_the_fastest_schedule(pkg):
+    for n, k, W in ((8192, 4096, 512), (16384, 8192, 256), (32768, 16384, 64)):
+        plan = pkg.Plan(n, k)
+        for op in (pkg.OP_ENCODE, pkg.OP_DECODE):
+            res = plan.autotune(W, op)
+            assert len(res) >= 1 and all(us > 0 for _, us in res)
+            best = min(res, key=lambda r: r[1])[0]
+            assert plan.schedule(op) == best
+        # the tuned plan still round-trips
+        src = synth.source(n, k, W)
+        pos = synth.received_positions(n, synth.erased_uniform(n + 3, n, k))
+        enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+        assert np.array_equal(pkg.to_host(plan.decode(pkg.to_device(enc[pos]), pos)), src)
+        assert plan.status() == 0
