@@ -115,7 +115,9 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *                       decode: n <= 16384, or n = 32768 with k <= n/2),
  *   FNT_RS_SCHED_SPLIT  radix-(n/4096) cross passes and 4096-point local
  *                       passes through the workspace (encode n > 8192,
- *                       decode n >= 16384).
+ *                       decode n >= 16384),
+ *   FNT_RS_SCHED_CPA    decode only: half-width tiles staged by cp.async,
+ *                       two CTAs per SM (n = 4096 or 8192, k <= n/2).
  * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else TILE
  * (encode up to n = 8192; decode wherever one CTA holds the codeword), else
  * SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
@@ -124,12 +126,13 @@ enum fnt_rs_sched {
   FNT_RS_SCHED_AUTO = 0,
   FNT_RS_SCHED_TMA = 1,
   FNT_RS_SCHED_TILE = 2,
-  FNT_RS_SCHED_SPLIT = 3
+  FNT_RS_SCHED_SPLIT = 3,
+  FNT_RS_SCHED_CPA = 4
 };
 
 typedef struct fnt_rs_tune_result_s {
   int sched; /* enum fnt_rs_sched */
-  float us;  /* median time of one call */
+  float us;  /* median time of one call, microseconds */
 } fnt_rs_tune_result;
 
 /* Forces the schedule of `op` (FNT_RS_OP_ENCODE or FNT_RS_OP_DECODE);

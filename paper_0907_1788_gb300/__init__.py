@@ -23,8 +23,8 @@ from ._lib import FntRsError, Group, LIB_PATH, Request, load  # noqa: F401
 
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
-SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT = 0, 1, 2, 3
-SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split"}
+SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT, SCHED_CPA = 0, 1, 2, 3, 4
+SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split", SCHED_CPA: "cpa"}
 
 E_RANGE = -7
 E_TIMEOUT = -8
@@ -319,8 +319,8 @@ def fnt_rs_autotune(plan, W: int, op: int, stream=None) -> list:
     """Times every schedule of `op` for W codewords; returns [(sched, us)], keeps the fastest."""
     from ._lib import TuneResult
 
-    buf = (TuneResult * 4)()
-    rc = int(load().fnt_rs_autotune(plan, W, op, buf, 4, _stream(stream)))
+    buf = (TuneResult * 8)()
+    rc = int(load().fnt_rs_autotune(plan, W, op, buf, 8, _stream(stream)))
     if rc < 0:
         _check(rc, "fnt_rs_autotune")
     return [(int(buf[i].sched), float(buf[i].us)) for i in range(rc)]

@@ -91,6 +91,25 @@ void launch_plan_fused(const PlanArgs& pa, cudaStream_t st) {
   count_launch();
 }
 
+template <class S, int WT, int NT>
+int launch_decode_cpa_t(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
+  auto kern = k_decode_cpa<S, WT, NT>;
+  constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
+  auto bytes = [&](int k) { return work + ((k * WT + 3) / 4 * 4) * 4 + kSchedBytes; };
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!done[dev & 63]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes(S::L / 2)) !=
+        cudaSuccess)
+      return -1;
+    done[dev & 63] = true;
+  }
+  kern<<<(a.W + WT - 1) / WT, NT, bytes(a.k), st>>>(a, pat32);
+  count_launch();
+  return 0;
+}
+
 template <int L>
 TileOps make_tile_ops() {
   using S = typename SchedFor<L>::type;
@@ -112,6 +131,10 @@ TileOps make_tile_ops() {
   }
   if constexpr (L >= 64 && (Lay<S, 1>::WORDS + L) * 4 <= 227 * 1024) {
     ops.plan_fused = &launch_plan_fused<S, 512>;
+  }
+  if constexpr (L == 4096 || L == 8192) {
+    ops.decode_cpa = &launch_decode_cpa_t<S, W1 / 2, 256>;
+    ops.wt_cpa = W1 / 2;
   }
   return ops;
 }

@@ -605,6 +605,81 @@ struct LoadStaged {
   }
 };
 
+// Steps 4-6 (Sec. II.B) on one staged tile of WT codewords, n = L, k <= n/2:
+// D1 = FNT with root r^-1 of u (pass 1 reads the stage through `load`),
+// truncation to j < k, D2 = FNT with root r, * ahat, D3 = FNT with root r^-1
+// to `store`; boundary passes of consecutive transforms fused.  `freed()` runs
+// (in every thread, after a barrier) once pass 1 has read the whole stage.
+template <class S, int WT, int NT, class LD, class ST, class F>
+__device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& store,
+                                                   const KArgs& a, F&& freed) {
+  using Y = Lay<S, WT>;
+  const uint32_t* tw1f = a.twf;
+  const uint32_t* tw1i = a.twi;
+  const uint32_t* __restrict__ ahat = a.ahat;
+  NopStore nop;
+  // D1 pass 1 (root r^-1) from the stage
+  dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
+  __syncthreads();
+  freed();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+    __syncthreads();
+  }
+  // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
+  {
+    constexpr int R = S::RL, B = ilog2(R);
+    for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+      const int c = t % WT, b = t / WT;
+      uint32_t* base = sm + b * Y::LAST_B + c;
+      uint32_t x[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = base[q * WT];
+      dft_reg<R, true>(x);
+      const int j0 = S::natural(b * R);
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
+      bitrev_regs<R>(x);
+      dft_reg<R, false>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
+    }
+  }
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
+    __syncthreads();
+  }
+  // last D2 pass * ahat + first D3 pass
+  {
+    constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
+    for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+      const int c = t % WT, i2 = t / WT;
+      uint32_t* base = sm + Y::addr(i2, c);
+      uint32_t x[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
+      twiddle_regs<R>(x, tw1f + i2 * R);
+      bitrev_regs<R>(x);
+      dft_reg<R, false>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
+      bitrev_regs<R>(x);
+      dft_reg<R, true>(x);
+      twiddle_regs<R>(x, tw1i + i2 * R);
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
+    }
+  }
+  __syncthreads();
+  if constexpr (S::NP == 3) {
+    dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+    __syncthreads();
+  }
+  dif_last<S, WT, NT, true>(sm, store);
+}
+
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
@@ -622,9 +697,6 @@ __global__ void __launch_bounds__(NT, 1)
   const int ntiles = (a.W + WT - 1) / WT;
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
-  const uint32_t* tw1f = a.twf;
-  const uint32_t* tw1i = a.twi;
-  const uint32_t* __restrict__ ahat = a.ahat;
   int tile = blockIdx.x;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -641,7 +713,6 @@ __global__ void __launch_bounds__(NT, 1)
   bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
   LoadStaged<WT> load{stage, pat32, 0u};
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
-  NopStore nop;
   while (tile < ntiles) {
     const bool ok = mbar_wait(bar, parity);
     if (__syncthreads_or(!ok)) {
@@ -654,82 +725,92 @@ __global__ void __launch_bounds__(NT, 1)
     }
     parity ^= 1u;
     store.col0 = tile * WT;
-    // D1 pass 1 (root r^-1) from the stage
-    dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // the stage is free: take over a pending CTA's tile and prefetch it
-      int nxt = clc_take(resp, cbar, cphase);
-      pending = false;
-      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
-      if (nxt >= 0 && nxt < ntiles) {
-        fence_proxy_async();
-        mbar_expect_tx(bar, tx_bytes);
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, nxt * WT, bx * box_rows, bar);
-        clc_request(resp, cbar);
-        pending = true;
-      } else {
-        nxt = ntiles;
+    decode_staged_tile<S, WT, NT>(sm, load, store, a, [&]() {
+      if (threadIdx.x == 0) {
+        // the stage is free: take over a pending CTA's tile and prefetch it
+        int nxt = clc_take(resp, cbar, cphase);
+        pending = false;
+        if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+        if (nxt >= 0 && nxt < ntiles) {
+          fence_proxy_async();
+          mbar_expect_tx(bar, tx_bytes);
+          for (int bx = 0; bx < nbox; ++bx)
+            tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, nxt * WT, bx * box_rows,
+                        bar);
+          clc_request(resp, cbar);
+          pending = true;
+        } else {
+          nxt = ntiles;
+        }
+        s_next = nxt;
       }
-      s_next = nxt;
-    }
-    if constexpr (S::NP == 3) {
-      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
-      __syncthreads();
-    }
-    // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
-    {
-      constexpr int R = S::RL, B = ilog2(R);
-      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
-        const int c = t % WT, b = t / WT;
-        uint32_t* base = sm + b * Y::LAST_B + c;
-        uint32_t x[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = base[q * WT];
-        dft_reg<R, true>(x);
-        const int j0 = S::natural(b * R);
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-          if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
-        bitrev_regs<R>(x);
-        dft_reg<R, false>(x);
-#pragma unroll
-        for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
-      }
-    }
+    });
     __syncthreads();
-    if constexpr (S::NP == 3) {
-      dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
-      __syncthreads();
-    }
-    // last D2 pass * ahat + first D3 pass
-    {
-      constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
-      for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
-        const int c = t % WT, i2 = t / WT;
-        uint32_t* base = sm + Y::addr(i2, c);
-        uint32_t x[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
-        twiddle_regs<R>(x, tw1f + i2 * R);
-        bitrev_regs<R>(x);
-        dft_reg<R, false>(x);
-#pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
-        bitrev_regs<R>(x);
-        dft_reg<R, true>(x);
-        twiddle_regs<R>(x, tw1i + i2 * R);
-#pragma unroll
-        for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
-      }
-    }
+    tile = s_next;
+  }
+  if (load.vmax > 65536u) atomicOr(a.status, ST_RANGE);
+  store.flush();
+}
+
+// ---------------------------------------------------------------------------
+// The same decode with half-width tiles staged by cp.async, two CTAs per SM:
+// the [k][WT] received tile (WT * 4 = 8 or 16 bytes per row, below TMA's
+// 16-byte row minimum for WT = 2) is copied by all threads; while one CTA
+// waits at a barrier or on shared memory the other computes.  Tiles are taken
+// over as in k_decode_tma.  Received rows must start 8-byte (WT = 2) or
+// 16-byte (WT = 4) aligned.
+// smem: work (Lay WORDS u32) | stage (k * WT u32) | barriers and cancel response.
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT>
+__global__ void __launch_bounds__(NT, 2)
+    k_decode_cpa(KArgs a, const uint32_t* __restrict__ pat32) {
+  static_assert(S::NP >= 2 && (WT == 2 || WT == 4), "");
+  using Y = Lay<S, WT>;
+  constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
+  extern __shared__ __align__(128) uint4 smem_raw[];
+  __shared__ int s_next;
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
+  const int k = a.k;
+  uint64_t* cbar = reinterpret_cast<uint64_t*>(stage + ((size_t)k * WT + 3) / 4 * 4);
+  uint4* resp = reinterpret_cast<uint4*>(cbar + 2);
+  const uint32_t* recv = static_cast<const uint32_t*>(a.in);
+  const size_t ld = a.ld_in;
+  const int ntiles = (a.W + WT - 1) / WT;
+  auto issue = [&](int t) {  // all threads: copy tile t's received rows
+    const int col0 = t * WT;
+    const int valid = min(WT, a.W - col0) * 4;
+    for (int r = threadIdx.x; r < k; r += NT)
+      cp_async<WT * 4>(stage + (size_t)r * WT, recv + (size_t)r * ld + col0, valid);
+    cp_async_commit();
+  };
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0) mbar_init(cbar, 1);
+  __syncthreads();
+  if (tile < ntiles) {
+    issue(tile);
+    if (threadIdx.x == 0) clc_request(resp, cbar);
+  }
+  uint32_t cphase = 0;
+  LoadStaged<WT> load{stage, pat32, 0u};
+  StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
+  while (tile < ntiles) {
+    cp_async_wait_all();
     __syncthreads();
-    if constexpr (S::NP == 3) {
-      dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
+    store.col0 = tile * WT;
+    decode_staged_tile<S, WT, NT>(sm, load, store, a, [&]() {
+      if (threadIdx.x == 0) {
+        int nxt = clc_take(resp, cbar, cphase);
+        if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+        s_next = (nxt >= 0 && nxt < ntiles) ? nxt : ntiles;
+      }
       __syncthreads();
-    }
-    dif_last<S, WT, NT, true>(sm, store);
+      // the stage is free: prefetch the taken-over tile, ask for the next one
+      if (s_next < ntiles) {
+        issue(s_next);
+        if (threadIdx.x == 0) clc_request(resp, cbar);
+      }
+    });
     __syncthreads();
     tile = s_next;
   }

@@ -274,6 +274,8 @@ bool sched_available(const fnt_rs_plan_s* p, int op, int s) {
   if (op == FNT_RS_OP_DECODE) {
     switch (s) {
       case FNT_RS_SCHED_TMA: return n >= 64 && n <= 8192 && !p->blocked && !p->no_tma;
+      case FNT_RS_SCHED_CPA: return tile_ops((int)n).decode_cpa != nullptr && !p->blocked &&
+                                    !p->split;
       case FNT_RS_SCHED_TILE: return !p->split;
       case FNT_RS_SCHED_SPLIT: return n >= 16384;
       default: return false;
@@ -695,6 +697,34 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
   return cuda_ok(cudaGetLastError());
 }
 
+// Decode with half-width tiles staged by cp.async, two CTAs per SM (packed
+// rows, n in {4096, 8192}, k <= n/2); returns 1 if not applicable.
+static int decode_cpa(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
+                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
+  if (p->split || p->blocked || p->n > 8192) return 1;
+  const TileOps& ops = tile_ops((int)p->n);
+  if (!ops.decode_cpa) return 1;
+  const size_t row_bytes = (size_t)ops.wt_cpa * 4;  // 8 or 16: the copy size
+  if (reinterpret_cast<uintptr_t>(recv) % row_bytes != 0 || (ld_recv * 4) % row_bytes != 0)
+    return 1;
+  KArgs a;
+  a.in = recv;
+  a.ld_in = ld_recv;
+  a.out = out;
+  a.ld_out = ld_out;
+  a.W = (int)W;
+  a.n = (int)p->n;
+  a.k = (int)p->k;
+  a.L = (int)p->n;
+  a.C = 1;
+  a.twf = p->tn.twf;
+  a.twi = p->tn.twi;
+  a.ahat = sl.ahat;
+  a.status = p->status;
+  if (ops.decode_cpa(a, sl.pat32, st) != 0) return 1;
+  return cuda_ok(cudaGetLastError());
+}
+
 // TMA-staged decode (one CTA per tile, cluster launch control; packed rows,
 // n <= tile limit, k <= n/2);
 // returns 1 if not applicable.
@@ -747,6 +777,10 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
   if (!slots && sched == FNT_RS_SCHED_TMA) {
     const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st);
     if (t != 1) return t;  // else (unaligned rows) the one-CTA tile below
+  }
+  if (!slots && sched == FNT_RS_SCHED_CPA) {
+    const int t = decode_cpa(p, sl, recv, ld_recv, out, ld_out, W, st);
+    if (t != 1) return t;
   }
   KArgs a;
   a.slots = slots;
@@ -1184,7 +1218,7 @@ int fnt_rs_autotune(fnt_rs_plan p, size_t W, int op, fnt_rs_tune_result* out, in
                     void* stream) {
   if (!p || W == 0 || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
   std::vector<int> cand;
-  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT})
+  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_CPA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT})
     if (sched_available(p, op, s)) cand.push_back(s);
   if (cand.empty()) return FNT_RS_E_ARG;
   cudaStream_t st = S(stream);

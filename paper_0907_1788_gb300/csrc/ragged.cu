@@ -316,10 +316,10 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
         w.second = w.second || rg.g.positions != nullptr;
       }
       for (auto& kv : widest) {
-        fnt_rs_tune_result res[4];
-        int rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_ENCODE, res, 4, stream);
+        fnt_rs_tune_result res[8];
+        int rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_ENCODE, res, 8, stream);
         if (rc >= 0 && kv.second.second)
-          rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_DECODE, res, 4, stream);
+          rc = fnt_rs_autotune(kv.first, kv.second.first, FNT_RS_OP_DECODE, res, 8, stream);
         if (rc < 0) return fail(rc);
         ++r->tuned;
       }

@@ -49,6 +49,9 @@ struct TileOps {
   Launch poly_level = nullptr;  // product-tree level (L = 2d)
   // log-domain pattern build (n = L) in one launch of D CTAs
   void (*plan_fused)(const PlanArgs&, cudaStream_t) = nullptr;
+  // decode with half-width tiles staged by cp.async, two CTAs per SM (k <= n/2)
+  int (*decode_cpa)(const KArgs&, const uint32_t* pat32, cudaStream_t) = nullptr;
+  int wt_cpa = 0;
 };
 
 // Registry filled by the instantiation units.

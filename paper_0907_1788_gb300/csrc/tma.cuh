@@ -61,6 +61,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Asynchronous global -> shared copy of BYTES (8 or 16) bytes of which the
+// first `valid` are read and the rest zero-filled (cp.async, LDGSTS).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int valid) {
+  static_assert(BYTES == 8 || BYTES == 16, "");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src),
+               "n"(BYTES), "r"(valid)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// waits for all of this thread's committed copies (a barrier then publishes them)
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Cluster launch control (sm_100 and later).  The TMA kernels are launched
 // with one CTA per tile; a running CTA asks the hardware to cancel the launch

@@ -97,7 +97,7 @@ def test_encode_concurrent_with_decode(pkg, decode_on_main):
 
 
 # ------------------------------------------------------------------ schedules
-@pytest.mark.parametrize("n,k,W", [(1024, 512, 256), (8192, 4096, 64), (8192, 6000, 32),
+@pytest.mark.parametrize("n,k,W", [(1024, 512, 256), (4096, 2000, 37), (8192, 4096, 64), (8192, 4096, 33), (8192, 6000, 32),
                                    (16384, 8192, 24), (16384, 12000, 8), (32768, 16384, 8)])
 def test_every_schedule_gives_the_same_words(pkg, n, k, W):
     seed = 17 * n + k
@@ -106,7 +106,7 @@ def test_every_schedule_gives_the_same_words(pkg, n, k, W):
     v = synth.received_uniform(seed + 2, k, W)
     plan = pkg.Plan(n, k)
     encs, decs = {}, {}
-    for s in (pkg.SCHED_TMA, pkg.SCHED_TILE, pkg.SCHED_SPLIT):
+    for s in (pkg.SCHED_TMA, pkg.SCHED_CPA, pkg.SCHED_TILE, pkg.SCHED_SPLIT):
         try:
             plan.set_schedule(pkg.OP_ENCODE, s)
         except pkg.FntRsError:
