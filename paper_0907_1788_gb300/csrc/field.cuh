@@ -140,4 +140,29 @@ __device__ __forceinline__ void dft_reg(uint32_t* x) {
   DifReg<R, 0, INV ? ((32 - e) & 31) : e>::run(x);
 }
 
+// The same DFT when the upper half of the input is known to be zero
+// (x[i] = 0 for i >= R/2): the first stage's butterflies reduce to
+// x[i + R/2] = x[i] * w^i (in Z/M, -a is the complement ~a).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg_lower(uint32_t* x) {
+  constexpr int e0 = Pow2Root<R>::e;
+  constexpr int E = INV ? ((32 - e0) & 31) : e0, H = R / 2;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const uint32_t a = x[i];
+    const int s = (E * i) & 31;
+    if (s == 0) {
+      x[i + H] = a;
+    } else if (s == 16) {
+      x[i + H] = ~a;
+    } else if (s > 16) {
+      x[i + H] = m_rot_rt(~a, s - 16);
+    } else {
+      x[i + H] = m_rot_rt(a, s);
+    }
+  }
+  DifReg<H, 0, (2 * E) & 31>::run(x);
+  DifReg<H, H, (2 * E) & 31>::run(x);
+}
+
 }  // namespace fntrs

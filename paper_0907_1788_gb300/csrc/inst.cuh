@@ -91,9 +91,9 @@ void launch_plan_fused(const PlanArgs& pa, cudaStream_t st) {
   count_launch();
 }
 
-template <class S, int WT, int NT>
-int launch_decode_cpa_t(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
-  auto kern = k_decode_cpa<S, WT, NT>;
+template <class S, int WT, int NT, bool HALF>
+int launch_decode_cpa_h(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
+  auto kern = k_decode_cpa<S, WT, NT, HALF>;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
   auto bytes = [&](int k) { return work + ((k * WT + 3) / 4 * 4) * 4 + kSchedBytes; };
   static bool done[64] = {};
@@ -108,6 +108,12 @@ int launch_decode_cpa_t(const KArgs& a, const uint32_t* pat32, cudaStream_t st) 
   kern<<<(a.W + WT - 1) / WT, NT, bytes(a.k), st>>>(a, pat32);
   count_launch();
   return 0;
+}
+
+template <class S, int WT, int NT>
+int launch_decode_cpa_t(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
+  if (2 * a.k == S::L) return launch_decode_cpa_h<S, WT, NT, true>(a, pat32, st);
+  return launch_decode_cpa_h<S, WT, NT, false>(a, pat32, st);
 }
 
 template <int L>
@@ -171,9 +177,9 @@ int launch_encode_tma_t(const KArgs& a, const uint32_t* twc, int rows_staged, in
 namespace fntrs {
 constexpr int decode_tma_max_rows(int L) { return L <= 256 ? L : L / 2; }
 
-template <class S, int WT, int NT>
-int launch_decode_tma_t(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
-  auto kern = k_decode_tma<S, WT, NT>;
+template <class S, int WT, int NT, bool HALF>
+int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  auto kern = k_decode_tma<S, WT, NT, HALF>;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
   const int smem = work + t.rows_staged * WT * 4 + kSchedBytes;
   static bool done[64] = {};
@@ -189,6 +195,13 @@ int launch_decode_tma_t(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st)
                                  *static_cast<const CUtensorMap*>(t.map));
   count_launch();
   return 0;
+}
+
+// k = n/2 exactly takes the pruned (HALF) variant
+template <class S, int WT, int NT>
+int launch_decode_tma_t(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
+  if (2 * a.k == S::L) return launch_decode_tma_h<S, WT, NT, true>(a, t, st);
+  return launch_decode_tma_h<S, WT, NT, false>(a, t, st);
 }
 
 template <int L>

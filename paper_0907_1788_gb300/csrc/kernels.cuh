@@ -610,7 +610,10 @@ struct LoadStaged {
 // truncation to j < k, D2 = FNT with root r, * ahat, D3 = FNT with root r^-1
 // to `store`; boundary passes of consecutive transforms fused.  `freed()` runs
 // (in every thread, after a barrier) once pass 1 has read the whole stage.
-template <class S, int WT, int NT, class LD, class ST, class F>
+// HALF (k = n/2 exactly): the truncation keeps the even registers of the
+// last D1 pass, so the first D2 pass sees a zero upper half, and D3 stores
+// only j < n/2; the compiler drops the butterfly halves nobody reads.
+template <class S, int WT, int NT, bool HALF, class LD, class ST, class F>
 __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& store,
                                                    const KArgs& a, F&& freed) {
   using Y = Lay<S, WT>;
@@ -636,12 +639,19 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
 #pragma unroll
       for (int q = 0; q < R; ++q) x[q] = base[q * WT];
       dft_reg<R, true>(x);
-      const int j0 = S::natural(b * R);
+      if constexpr (HALF) {
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
-      bitrev_regs<R>(x);
-      dft_reg<R, false>(x);
+        for (int q = 1; q < R; q += 2) x[q] = 0u;  // j = j0 + (L/R) bitrev(q) >= n/2
+        bitrev_regs<R>(x);
+        dft_reg_lower<R, false>(x);
+      } else {
+        const int j0 = S::natural(b * R);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (j0 + (S::L / R) * bitrev(q, B) >= a.k) x[q] = 0u;
+        bitrev_regs<R>(x);
+        dft_reg<R, false>(x);
+      }
 #pragma unroll
       for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
     }
@@ -677,10 +687,10 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
     __syncthreads();
   }
-  dif_last<S, WT, NT, true>(sm, store);
+  dif_last_sel<S, WT, NT, true, HALF>(sm, store);
 }
 
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
                  const __grid_constant__ CUtensorMap trecv) {
@@ -725,7 +735,7 @@ __global__ void __launch_bounds__(NT, 1)
     }
     parity ^= 1u;
     store.col0 = tile * WT;
-    decode_staged_tile<S, WT, NT>(sm, load, store, a, [&]() {
+    decode_staged_tile<S, WT, NT, HALF>(sm, load, store, a, [&]() {
       if (threadIdx.x == 0) {
         // the stage is free: take over a pending CTA's tile and prefetch it
         int nxt = clc_take(resp, cbar, cphase);
@@ -761,7 +771,7 @@ __global__ void __launch_bounds__(NT, 1)
 // 16-byte (WT = 4) aligned.
 // smem: work (Lay WORDS u32) | stage (k * WT u32) | barriers and cancel response.
 // ---------------------------------------------------------------------------
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 2)
     k_decode_cpa(KArgs a, const uint32_t* __restrict__ pat32) {
   static_assert(S::NP >= 2 && (WT == 2 || WT == 4), "");
@@ -798,7 +808,7 @@ __global__ void __launch_bounds__(NT, 2)
     cp_async_wait_all();
     __syncthreads();
     store.col0 = tile * WT;
-    decode_staged_tile<S, WT, NT>(sm, load, store, a, [&]() {
+    decode_staged_tile<S, WT, NT, HALF>(sm, load, store, a, [&]() {
       if (threadIdx.x == 0) {
         int nxt = clc_take(resp, cbar, cphase);
         if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);

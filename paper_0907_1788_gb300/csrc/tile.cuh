@@ -152,8 +152,8 @@ __device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict
 }
 
 // Last DIF pass: slots -> storer, store(j, c, v) with j the spectrum index.
-template <class S, int WT, int NT, bool INV, class Store>
-__device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
+template <class S, int WT, int NT, bool INV, bool LOWER, class Store>
+__device__ __forceinline__ void dif_last_sel(uint32_t* sm, Store& store) {
   static_assert(S::NP >= 2, "");
   using Y = Lay<S, WT>;
   constexpr int R = S::RL, B = ilog2(R);
@@ -166,8 +166,17 @@ __device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
     dft_reg<R, INV>(x);
     const int j0 = S::natural(b * R);
 #pragma unroll
-    for (int q = 0; q < R; ++q) store(j0 + (S::L / R) * bitrev(q, B), c, x[q]);
+    for (int q = 0; q < R; ++q)
+      if (!LOWER || (q & 1) == 0) store(j0 + (S::L / R) * bitrev(q, B), c, x[q]);
   }
+}
+
+template <class S, int WT, int NT, bool INV, class Store>
+// LOWER: only spectrum indices j < L/2 are wanted (register q holds
+// j = j0 + (L/R) bitrev(q) with j0 < L/R, so those are the even q); the
+// others are neither computed nor stored.
+__device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
+  dif_last_sel<S, WT, NT, INV, false>(sm, store);
 }
 
 // Last DIF pass writing back into the slots (for a following DIT sequence).
