@@ -309,6 +309,23 @@ def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
     return out
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's value (a timing), or x itself without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(src_bytes_per_rank: int, world: int, ms: float) -> float:
+    """Source GB/s of the whole job: every rank (a replica) decodes its own batch."""
+    return world * src_bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -440,10 +457,7 @@ def run_gpu(args):
         dist.barrier()
     launches = pkg.fnt_rs_launch_count() - launches0
     ms_step = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = max_over_ranks(ms_step, dev)
     assert np.array_equal(pkg.to_host(out), cfg.source()), "round trip failed (timed)"
     assert plan.status() == 0
 
@@ -462,7 +476,7 @@ def run_gpu(args):
     assert np.array_equal(pkg.to_host(out), cfg.source()), "round trip failed (serial)"
 
     src_bytes = k * W * 2
-    value = world * src_bytes / (ms_step * 1e-3) / 1e9
+    value = whole_job_gbs(src_bytes, world, ms_step)
     enc_ms, pat_ms, dec_ms = (statistics.mean(t_enc), statistics.mean(t_pat),
                               statistics.mean(t_dec))
 
