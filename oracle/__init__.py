@@ -15,4 +15,5 @@ Two layers:
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants or brute force (see each test's docstring).
 """
-from .core import build, lib_path, root, encode, encode_rows, decode, pattern, dft, max_threads, P  # noqa: F401
+from .core import (build, lib_path, root, encode, encode_rows, decode, pattern, dft,  # noqa: F401
+                   max_threads, P, interpolate, encode_sys, decode_sys)

@@ -64,6 +64,13 @@ def _load():
             lib.orc_decode.argtypes = [u32, u32, u32, vp, sz, vp, u32, vp, sz, sz,
                                        ctypes.POINTER(i32), i32]
             lib.orc_decode.restype = i32
+            lib.orc_interpolate.argtypes = [u32, u32, u32, vp, sz, vp, u32, vp, sz, sz, i32]
+            lib.orc_interpolate.restype = i32
+            lib.orc_encode_sys.argtypes = [u32, u32, u32, vp, sz, u32, vp, sz, sz, i32]
+            lib.orc_encode_sys.restype = i32
+            lib.orc_decode_sys.argtypes = [u32, u32, u32, vp, sz, vp, u32, vp, sz, sz,
+                                           ctypes.POINTER(i32), i32]
+            lib.orc_decode_sys.restype = i32
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = i32
             _lib = lib
@@ -148,4 +155,50 @@ def decode(recv: np.ndarray, positions, n: int, k: int, root_: int = 0, threads:
                             ctypes.byref(flag), threads or max_threads())
     if rc not in (0, -3):
         raise ValueError(f"orc_decode failed: {rc}")
+    return out, bool(flag.value)
+
+
+def interpolate(recv: np.ndarray, positions, n: int, k: int, root_: int = 0,
+                threads: int = 0) -> np.ndarray:
+    """Coefficients of the interpolant of the first k received points: [k][W] uint32 in [0, p)."""
+    recv = np.ascontiguousarray(recv, dtype=np.uint32)
+    pos = np.ascontiguousarray(positions, dtype=np.uint32)
+    npos, W = recv.shape
+    if len(pos) != npos:
+        raise ValueError("one received row per position")
+    out = np.empty((k, W), dtype=np.uint32)
+    rc = _load().orc_interpolate(n, k, root_, _ptr(recv), W, _ptr(pos), npos, _ptr(out), W, W,
+                                 threads or max_threads())
+    if rc:
+        raise ValueError(f"orc_interpolate failed: {rc}")
+    return out
+
+
+def encode_sys(src: np.ndarray, n: int, n_out: int = 0, root_: int = 0,
+               threads: int = 0) -> np.ndarray:
+    """Systematic code: [n_out][W] uint32 whose first k rows are ``src`` ([k][W] uint16)."""
+    src = np.ascontiguousarray(src, dtype=np.uint16)
+    k, W = src.shape
+    n_out = n_out or n
+    out = np.empty((n_out, W), dtype=np.uint32)
+    rc = _load().orc_encode_sys(n, k, root_, _ptr(src), W, n_out, _ptr(out), W, W,
+                                threads or max_threads())
+    if rc:
+        raise ValueError(f"orc_encode_sys failed: {rc}")
+    return out
+
+
+def decode_sys(recv: np.ndarray, positions, n: int, k: int, root_: int = 0, threads: int = 0):
+    """Systematic decode: (source [k][W] uint16, range_flag) from the first k received points."""
+    recv = np.ascontiguousarray(recv, dtype=np.uint32)
+    pos = np.ascontiguousarray(positions, dtype=np.uint32)
+    npos, W = recv.shape
+    if len(pos) != npos:
+        raise ValueError("one received row per position")
+    out = np.empty((k, W), dtype=np.uint16)
+    flag = ctypes.c_int(0)
+    rc = _load().orc_decode_sys(n, k, root_, _ptr(recv), W, _ptr(pos), npos, _ptr(out), W, W,
+                                ctypes.byref(flag), threads or max_threads())
+    if rc not in (0, -3):
+        raise ValueError(f"orc_decode_sys failed: {rc}")
     return out, bool(flag.value)

@@ -22,6 +22,12 @@
  *                                                                   rewrite and derivative identity)
  *   orc_decode       P(x) = sum_i v_i A_i(x) / A_i(x_i) with
  *                    A_i = A / (x - x_i) by synthetic division     (Sec. II.B, Lagrange formula)
+ *   orc_interpolate  the same P with all its coefficients kept as elements of F_p
+ *   orc_encode_sys   systematic code: intermediate symbols = the interpolant of the source at
+ *                    the first k points r^0..r^(k-1), encoded = its values at r^j
+ *                    (Sec. II, "Toward a systematic code"); j < n_out (puncturing, Sec. II.B)
+ *   orc_decode_sys   systematic decode: interpolate the first k received points, then the
+ *                    source is the interpolant's value at r^0..r^(k-1) (same section)
  *
  * Readings where the paper is silent: the first k entries of `positions`
  * are the interpolation points (Sec. II.B, "first k evaluation points
@@ -251,6 +257,118 @@ int orc_decode(uint32_t n, uint32_t k, uint32_t root, const uint32_t* recv, size
   free(A);
   free(w);
   if (range_flag) *range_flag = flag;
+  return flag ? ORC_RANGE : ORC_OK;
+}
+
+/*
+ * Lagrange interpolation as orc_decode, with the coefficients of P kept as
+ * elements of F_p (u32 in [0, 65536]): coef [k][ld_coef].
+ */
+int orc_interpolate(uint32_t n, uint32_t k, uint32_t root, const uint32_t* recv, size_t ld_recv,
+                    const uint32_t* positions, uint32_t npos, uint32_t* coef, size_t ld_coef,
+                    size_t W, int nthreads) {
+  if (!is_pow2_n(n) || k < 1 || k > n || !recv || !coef) return ORC_ARG;
+  uint32_t r = root ? root : orc_root(n);
+  uint32_t* A = (uint32_t*)malloc(((size_t)k + 1) * sizeof(uint32_t));
+  uint32_t* w = (uint32_t*)malloc((size_t)k * sizeof(uint32_t));
+  if (!A || !w) { free(A); free(w); return ORC_ARG; }
+  int rc = orc_pattern(n, k, r, positions, npos, A, NULL, w);
+  if (rc) { free(A); free(w); return rc; }
+  (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (long long c = 0; c < (long long)W; ++c) {
+    uint32_t* P = (uint32_t*)calloc(k, sizeof(uint32_t));
+    uint32_t* Q = (uint32_t*)malloc((size_t)k * sizeof(uint32_t));
+    for (uint32_t i = 0; i < k; ++i) {
+      uint32_t xi = orc_pow(r, positions[i]);
+      Q[k - 1] = A[k];
+      for (uint32_t j = k - 1; j >= 1; --j) Q[j - 1] = orc_add(A[j], orc_mul(xi, Q[j]));
+      uint32_t cf = orc_mul(recv[(size_t)i * ld_recv + c] % ORC_P, w[i]);
+      for (uint32_t j = 0; j < k; ++j) P[j] = orc_add(P[j], orc_mul(cf, Q[j]));
+    }
+    for (uint32_t j = 0; j < k; ++j) coef[(size_t)j * ld_coef + c] = P[j];
+    free(P);
+    free(Q);
+  }
+  free(A);
+  free(w);
+  return ORC_OK;
+}
+
+/* Value at r^j (j < n_rows) of the polynomial with coefficients coef [k][ld] (Horner). */
+static void eval_rows(uint32_t r, uint32_t k, const uint32_t* coef, size_t ld_coef,
+                      uint32_t n_rows, uint32_t* out, size_t ld_out, size_t W, int nthreads) {
+  (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (long long c = 0; c < (long long)W; ++c) {
+    uint32_t x = 1;
+    for (uint32_t j = 0; j < n_rows; ++j) {
+      uint32_t acc = 0;
+      for (uint32_t i = k; i-- > 0;) acc = orc_add(orc_mul(acc, x), coef[(size_t)i * ld_coef + c]);
+      out[(size_t)j * ld_out + c] = acc;
+      x = orc_mul(x, r);
+    }
+  }
+}
+
+/*
+ * Systematic encode: i(x) = the interpolant of s_0..s_{k-1} at r^0..r^(k-1),
+ * enc[j] = i(r^j) for j < n_out (so enc[j] = s_j for j < k).
+ * src [k][ld_src] u16, enc [n_out][ld_enc] u32; k <= n_out <= n.
+ */
+int orc_encode_sys(uint32_t n, uint32_t k, uint32_t root, const uint16_t* src, size_t ld_src,
+                   uint32_t n_out, uint32_t* enc, size_t ld_enc, size_t W, int nthreads) {
+  if (!is_pow2_n(n) || k < 1 || k > n || n_out < k || n_out > n || !src || !enc) return ORC_ARG;
+  uint32_t r = root ? root : orc_root(n);
+  uint32_t* pos = (uint32_t*)malloc((size_t)k * sizeof(uint32_t));
+  uint32_t* vals = (uint32_t*)malloc((size_t)k * W * sizeof(uint32_t));
+  uint32_t* coef = (uint32_t*)malloc((size_t)k * W * sizeof(uint32_t));
+  int rc = ORC_ARG;
+  if (pos && vals && coef) {
+    for (uint32_t i = 0; i < k; ++i) pos[i] = i;
+    for (size_t i = 0; i < k; ++i)
+      for (size_t c = 0; c < W; ++c) vals[i * W + c] = src[i * ld_src + c];
+    rc = orc_interpolate(n, k, r, vals, W, pos, k, coef, W, W, nthreads);
+    if (rc == ORC_OK) eval_rows(r, k, coef, W, n_out, enc, ld_enc, W, nthreads);
+  }
+  free(pos);
+  free(vals);
+  free(coef);
+  return rc;
+}
+
+/*
+ * Systematic decode: i(x) = the interpolant of the first k received points,
+ * out[j] = i(r^j) for j < k (u16; a value 65536 is written as 0 and sets
+ * *range_flag).  recv [npos][ld_recv] u32 as for orc_decode.
+ */
+int orc_decode_sys(uint32_t n, uint32_t k, uint32_t root, const uint32_t* recv, size_t ld_recv,
+                   const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
+                   size_t W, int* range_flag, int nthreads) {
+  if (!is_pow2_n(n) || k < 1 || k > n || !recv || !out) return ORC_ARG;
+  uint32_t r = root ? root : orc_root(n);
+  uint32_t* coef = (uint32_t*)malloc((size_t)k * W * sizeof(uint32_t));
+  uint32_t* vals = (uint32_t*)malloc((size_t)k * W * sizeof(uint32_t));
+  if (!coef || !vals) { free(coef); free(vals); return ORC_ARG; }
+  int rc = orc_interpolate(n, k, r, recv, ld_recv, positions, npos, coef, W, W, nthreads);
+  int flag = 0;
+  if (rc == ORC_OK) {
+    eval_rows(r, k, coef, W, k, vals, W, W, nthreads);
+    for (size_t j = 0; j < k; ++j)
+      for (size_t c = 0; c < W; ++c) {
+        const uint32_t v = vals[j * W + c];
+        if (v == 65536u) { flag = 1; out[j * ld_out + c] = 0; }
+        else out[j * ld_out + c] = (uint16_t)v;
+      }
+  }
+  free(coef);
+  free(vals);
+  if (range_flag) *range_flag = flag;
+  if (rc) return rc;
   return flag ? ORC_RANGE : ORC_OK;
 }
 
