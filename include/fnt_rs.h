@@ -71,7 +71,9 @@ enum fnt_rs_op {
   FNT_RS_OP_DECODE = 1,
   FNT_RS_OP_FNT = 2,
   FNT_RS_OP_ENCODE_HOST = 3,    /* fnt_rs_encode_host staging */
-  FNT_RS_OP_DECODE_HOST = 4     /* fnt_rs_decode_host staging */
+  FNT_RS_OP_DECODE_HOST = 4,    /* fnt_rs_decode_host staging */
+  FNT_RS_OP_ENCODE_SYS = 5,     /* fnt_rs_encode_sys */
+  FNT_RS_OP_DECODE_SYS = 6      /* fnt_rs_decode_sys */
 };
 
 typedef struct fnt_rs_plan_s* fnt_rs_plan;
@@ -254,6 +256,43 @@ int fnt_rs_decode_host(fnt_rs_plan plan, const uint32_t* h_recv, const uint32_t*
 #define FNT_RS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int fnt_rs_encode_noalloc(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t* enc,
                           size_t ld_enc, size_t W, void* stream);
+
+/*
+ * Punctured code (Sec. II.B: a length that is not a power of two is a
+ * puncturing of the next power of two).  Keeps the first n_out positions of
+ * the plan's length-n code, k <= n_out <= n: fnt_rs_encode and
+ * fnt_rs_encode_sys then write n_out rows (the workspace grows by n * W * 4
+ * bytes for the rows dropped), positions passed to the decoders must be below
+ * n_out, and fnt_rs_decode_full (which needs every position) returns
+ * FNT_RS_E_ARG.  n_out = n restores the full code.  FNT_RS_E_ARG if n_out is
+ * out of range.
+ */
+int fnt_rs_plan_set_length(fnt_rs_plan plan, uint32_t n_out);
+
+/*
+ * Systematic code (the paper's "Toward a systematic code" section).  Encode:
+ * the k source values of every codeword are interpolated at the first k
+ * positions r^0..r^(k-1), which gives k intermediate symbols (coefficients of
+ * a polynomial of degree < k over F_p); their length-n transform is the
+ * codeword, whose first k rows are therefore the source itself.
+ * src [k][ld_src] u16, enc [n_out][ld_enc] u32 (device).  Decode: the
+ * intermediate symbols are interpolated from the first k of `positions` (as
+ * fnt_rs_decode does) and transformed again; rows 0..k-1 of the result are
+ * the source, written to out [k][ld_out] u16 (a value 65536 is written as 0
+ * and raises FNT_RS_E_RANGE in the status word).  When the first k positions
+ * are exactly 0, 1, ..., k-1 the decoder copies the received rows instead.
+ * recv [npos][ld_recv] u32 (row i = positions[i]), positions on the host.
+ * workspace: device, fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_ENCODE_SYS /
+ * FNT_RS_OP_DECODE_SYS) bytes (2 * n * W * 4 plus the decode's own); the
+ * intermediate-symbol pattern is built on the first call (synchronising
+ * `stream` once).  Default root only (FNT_RS_E_ROOT otherwise).  Enqueued on
+ * `stream`.
+ */
+int fnt_rs_encode_sys(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                      size_t ld_enc, size_t W, void* workspace, void* stream);
+int fnt_rs_decode_sys(fnt_rs_plan plan, const uint32_t* recv, size_t ld_recv,
+                      const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
+                      size_t W, void* workspace, void* stream);
 
 /*
  * Reads the plan's device status word (synchronising `stream`), clears it and

@@ -23,6 +23,7 @@ from ._lib import FntRsError, Group, LIB_PATH, Request, load  # noqa: F401
 
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
+OP_ENCODE_SYS, OP_DECODE_SYS = 5, 6
 SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT, SCHED_CPA = 0, 1, 2, 3, 4
 SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split", SCHED_CPA: "cpa"}
 
@@ -304,6 +305,31 @@ def fnt_rs_baseline_replay(reqs, arrivals, stream=None):
     return lat, wall.value
 
 
+def fnt_rs_plan_set_length(plan, n_out: int) -> None:
+    _check(load().fnt_rs_plan_set_length(plan, n_out), "fnt_rs_plan_set_length")
+
+
+def fnt_rs_encode_sys(plan, src: torch.Tensor, enc: torch.Tensor, workspace=None, stream=None):
+    W, ld_src = _cols(src)
+    W2, ld_enc = _cols(enc)
+    if W2 != W:
+        raise ValueError("src and enc must have the same number of columns")
+    _check(load().fnt_rs_encode_sys(plan, _ptr(src), ld_src, _ptr(enc), ld_enc, W,
+                                    _ptr(workspace), _stream(stream)), "fnt_rs_encode_sys")
+
+
+def fnt_rs_decode_sys(plan, recv: torch.Tensor, positions, out: torch.Tensor, workspace=None,
+                      stream=None):
+    W, ld_recv = _cols(recv)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("recv and out must have the same number of columns")
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode_sys(plan, _ptr(recv), ld_recv, pos.ctypes.data, len(pos),
+                                    _ptr(out), ld_out, W, _ptr(workspace), _stream(stream)),
+           "fnt_rs_decode_sys")
+
+
 def fnt_rs_set_schedule(plan, op: int, sched: int) -> None:
     _check(load().fnt_rs_set_schedule(plan, op, sched), "fnt_rs_set_schedule")
 
@@ -379,7 +405,8 @@ class Plan:
     def encode(self, src: torch.Tensor, out=None, stream=None):
         W = src.shape[1]
         if out is None:
-            out = torch.empty((self.n, W), dtype=torch.int32, device=src.device)
+            out = torch.empty((getattr(self, "n_out", self.n), W), dtype=torch.int32,
+                              device=src.device)
         fnt_rs_encode(self.handle, src, out, self.workspace(W, OP_ENCODE), stream)
         return out
 
@@ -417,6 +444,27 @@ class Plan:
 
     def status(self, stream=None) -> int:
         return fnt_rs_status(self.handle, stream)
+
+    def set_length(self, n_out: int) -> None:
+        """Puncture the code to its first n_out positions (n_out = n: the full code)."""
+        fnt_rs_plan_set_length(self.handle, n_out)
+        self.n_out = n_out
+
+    def encode_sys(self, src: torch.Tensor, out=None, stream=None):
+        W = src.shape[1]
+        if out is None:
+            out = torch.empty((getattr(self, "n_out", self.n), W), dtype=torch.int32,
+                              device=src.device)
+        fnt_rs_encode_sys(self.handle, src, out, self.workspace(W, OP_ENCODE_SYS), stream)
+        return out
+
+    def decode_sys(self, recv: torch.Tensor, positions, out=None, stream=None):
+        W = recv.shape[1]
+        if out is None:
+            out = torch.empty((self.k, W), dtype=torch.int16, device=recv.device)
+        fnt_rs_decode_sys(self.handle, recv, positions, out, self.workspace(W, OP_DECODE_SYS),
+                          stream)
+        return out
 
     def autotune(self, W: int, op: int, stream=None) -> list:
         return fnt_rs_autotune(self.handle, W, op, stream)

@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
 SOURCES = ["plan.cu", "pattern.cu", "inst_small.cu", "inst_mid.cu", "inst_big.cu",
-           "inst_huge.cu", "inst_split.cu", "noalloc.cu", "ragged.cu", "ragged_kernel.cu", "server.cu"]
+           "inst_huge.cu", "inst_split.cu", "noalloc.cu", "ragged.cu", "ragged_kernel.cu", "server.cu",
+           "systematic.cu"]
 
 
 def nvcc() -> str:

@@ -74,6 +74,9 @@ struct fnt_rs_plan_s {
   fntrs::PatternSlot slots[fntrs::kPatternSlots];
   int current = -1;
   uint64_t clock = 0;
+  uint32_t n_out = 0;         // code length after puncturing (k <= n_out <= n)
+  fntrs::PatternSlot sys;     // pattern of positions 0..k-1 (systematic code), built on first use
+  bool sys_ready = false;
 };
 
 namespace fntrs {
@@ -90,9 +93,19 @@ bool sched_available(const fnt_rs_plan_s* p, int op, int sched);
 int sched_effective(const fnt_rs_plan_s* p, int op);
 int fnt_nbuf(const fnt_rs_plan_s* p);
 size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf);
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+// workspace of the systematic encode / decode (systematic.cu)
+size_t sys_workspace_bytes(const fnt_rs_plan_s* p, size_t W);
 int get_tables(int L, Tables* out);
 uint32_t hinv(uint32_t a);
 int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos);
+// find or build the pattern of the first k positions (p->current)
+int prepare_pattern(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, cudaStream_t st);
+// length-n transform of W columns (forward or n^-1-scaled inverse), in column
+// chunks through `work` (fnt_columns_work_bytes) when n exceeds the tile limit
+int fnt_columns(fnt_rs_plan_s* p, const uint32_t* in, size_t ld_in, uint32_t* out,
+                size_t ld_out, size_t W, bool inverse, void* work, cudaStream_t st);
+size_t fnt_columns_work_bytes(const fnt_rs_plan_s* p, size_t W);
 // build the pattern of the positions already uploaded to sl.pos_d (or, for
 // the one-launch build, of the device-readable positions `pos`)
 int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st,
@@ -107,9 +120,10 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
                        size_t ld_enc, size_t W, uint32_t* work, cudaStream_t st);
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
               size_t W, void* workspace, cudaStream_t st);
-// decode with explicit pattern tables (slots != 0: row z of recv is position z)
+// decode with explicit pattern tables (slots != 0: row z of recv is position z);
+// with out32 the coefficients go there as u32 (ld_out) and `out` is unused
 int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
-                     cudaStream_t st, int slots);
+                     cudaStream_t st, int slots, uint32_t* out32 = nullptr);
 
 }  // namespace fntrs

@@ -43,6 +43,7 @@ struct KArgs {
   int n = 0, k = 0, L = 0, C = 1, h = 0;
   int row_limit = 0;  // input rows >= row_limit read as zero
   int out_limit = 0;  // output rows >= out_limit not written
+  void* out32 = nullptr;  // decode: coefficients as u32 in [0, p) here instead of 16-bit symbols
   uint32_t scale = 1;
   const uint32_t* twf = nullptr;   // per-pass tables of the L-schedule, forward root
   const uint32_t* twi = nullptr;   // same, inverse root

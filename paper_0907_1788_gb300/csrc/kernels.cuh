@@ -171,7 +171,10 @@ struct StoreLocal {
     } else if constexpr (MODE == LM_OUT16) {
       if ((int)row < a.out_limit) {
         if (a.scale != 1u) v = m_mul(v, a.scale);
-        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
+        if (a.out32)
+          static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
+        else
+          static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
       }
     } else if constexpr (MODE == LM_SPLIT) {
       if ((int)row < a.h)
@@ -189,7 +192,10 @@ struct StoreLocal {
       if ((int)row < a.out_limit) {
         if ((int)row >= a.h)
           v = m_add(v, static_cast<const uint32_t*>(a.in2)[(row - a.h) * a.ld_work + col]);
-        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
+        if (a.out32)
+          static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
+        else
+          static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
       }
     }
   }
@@ -434,21 +440,28 @@ __global__ void __launch_bounds__(256) k_cross(KArgs a) {
 // The boundary passes of consecutive transforms act on the same register
 // groups and are fused.
 // ---------------------------------------------------------------------------
+// With out32 set the coefficients go there as u32 in [0, p) (all of F_p, as
+// the systematic code's intermediate symbols need) instead of 16-bit symbols.
 template <int WT>
 struct StoreOut16 {
   uint16_t* out;
+  uint32_t* out32;
   size_t ld;
   int* status;
   int col0, W, k;
   uint32_t bad;
   static __device__ __forceinline__ StoreOut16 make(const KArgs& a, int tx, int ty) {
     (void)ty;
-    return StoreOut16{static_cast<uint16_t*>(a.out), a.ld_out, a.status, tx * WT, a.W, a.k, 0u};
+    return StoreOut16{static_cast<uint16_t*>(a.out), static_cast<uint32_t*>(a.out32), a.ld_out,
+                      a.status, tx * WT, a.W, a.k, 0u};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
     if (col >= W || j >= k) return;
-    out[(size_t)j * ld + col] = to_symbol(v, bad);
+    if (out32)
+      out32[(size_t)j * ld + col] = m_to_p(v);
+    else
+      out[(size_t)j * ld + col] = to_symbol(v, bad);
   }
   __device__ __forceinline__ void flush() const {
     if (bad > 65535u) atomicOr(status, ST_RANGE);
@@ -1003,7 +1016,12 @@ __device__ __forceinline__ void decode_split_smem(const KArgs& a, int tx) {
           const int j = j0 + (S::L / R) * d;
           uint32_t v = x[d];
           if (d >= HR) v = m_add(v, y[d - HR]);
-          if (j < k) out[(size_t)j * a.ld_out + col] = to_symbol(v, bad);
+          if (j < k) {
+            if (a.out32)
+              static_cast<uint32_t*>(a.out32)[(size_t)j * a.ld_out + col] = m_to_p(v);
+            else
+              out[(size_t)j * a.ld_out + col] = to_symbol(v, bad);
+          }
         }
       }
     }

@@ -305,6 +305,8 @@ int enc_nbuf_max(const fnt_rs_plan_s* p) { return p->n > 8192 ? 1 : 0; }
 int dec_nbuf_max(const fnt_rs_plan_s* p) { return p->n >= 16384 ? (p->blocked ? 4 : 2) : 0; }
 int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
 
+static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
 size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf) {
   if (nbuf == 0 || W == 0) return 0;
   const size_t wc = std::min(W, split_chunk(p->n, nbuf));
@@ -540,7 +542,7 @@ int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npo
   if (npos < p->k) return FNT_RS_E_POSITIONS;
   std::vector<uint8_t> seen(p->n, 0);
   for (uint32_t i = 0; i < npos; ++i) {
-    if (pos[i] >= p->n || seen[pos[i]]) return FNT_RS_E_POSITIONS;
+    if (pos[i] >= p->n_out || seen[pos[i]]) return FNT_RS_E_POSITIONS;
     seen[pos[i]] = 1;
   }
   return FNT_RS_OK;
@@ -589,6 +591,10 @@ static int prepare(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, c
   sl.last_use = p->clock;
   p->current = victim;
   return FNT_RS_OK;
+}
+
+int prepare_pattern(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, cudaStream_t st) {
+  return prepare(p, positions, npos, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -700,7 +706,8 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
 // Decode with half-width tiles staged by cp.async, two CTAs per SM (packed
 // rows, n in {4096, 8192}, k <= n/2); returns 1 if not applicable.
 static int decode_cpa(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
-                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
+                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st,
+                      uint32_t* out32) {
   if (p->split || p->blocked || p->n > 8192) return 1;
   const TileOps& ops = tile_ops((int)p->n);
   if (!ops.decode_cpa) return 1;
@@ -721,6 +728,7 @@ static int decode_cpa(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   a.twi = p->tn.twi;
   a.ahat = sl.ahat;
   a.status = p->status;
+  a.out32 = out32;
   if (ops.decode_cpa(a, sl.pat32, st) != 0) return 1;
   return cuda_ok(cudaGetLastError());
 }
@@ -729,7 +737,8 @@ static int decode_cpa(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
 // n <= tile limit, k <= n/2);
 // returns 1 if not applicable.
 static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
-                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st) {
+                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st,
+                      uint32_t* out32) {
   if (p->no_tma || p->split || p->blocked || p->n < 64 || p->n > 8192) return 1;
   if ((reinterpret_cast<uintptr_t>(recv) % 16) != 0 || (ld_recv * 4) % 16 != 0) return 1;
   auto fn = tmap_encode_fn();
@@ -760,6 +769,7 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   a.twi = p->tn.twi;
   a.ahat = sl.ahat;
   a.status = p->status;
+  a.out32 = out32;
   TmaDecodeArgs t;
   t.pat32 = sl.pat32;
   t.rows_staged = rows_staged;
@@ -772,14 +782,14 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
 
 int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
-                     cudaStream_t st, int slots) {
+                     cudaStream_t st, int slots, uint32_t* out32) {
   const int sched = sched_effective(p, FNT_RS_OP_DECODE);
   if (!slots && sched == FNT_RS_SCHED_TMA) {
-    const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st);
+    const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st, out32);
     if (t != 1) return t;  // else (unaligned rows) the one-CTA tile below
   }
   if (!slots && sched == FNT_RS_SCHED_CPA) {
-    const int t = decode_cpa(p, sl, recv, ld_recv, out, ld_out, W, st);
+    const int t = decode_cpa(p, sl, recv, ld_recv, out, ld_out, W, st, out32);
     if (t != 1) return t;
   }
   KArgs a;
@@ -795,6 +805,7 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
   a.ahat = sl.ahat;
   a.ahat2 = sl.ahat2;
   a.status = p->status;
+  a.out32 = out32;
   if (sched != FNT_RS_SCHED_SPLIT) {
     const TileOps& ops = tile_ops((int)p->n);
     a.W = (int)W;
@@ -934,6 +945,7 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
   p->split = n > (uint32_t)kTileMaxL || (n == (uint32_t)kTileMaxL && 2 * k > n);
   p->C = p->split ? (int)(n / kLocalL) : 1;
   p->blocked = k > n / 2;
+  p->n_out = n;
   p->C_local = n > 8192 ? (int)(n / kLocalL) : 1;
   int rc = get_tables((int)n, &p->tn);
   if (!rc && n > 8192) rc = get_tables(kLocalL, &p->tl);
@@ -1027,18 +1039,23 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   cudaFree(p->twc);
   cudaFree(p->ghat);
   for (auto& sl : p->slots) free_pattern_tables(sl);
+  free_pattern_tables(p->sys);
   delete p;
 }
 
 size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
   if (!p) return 0;
   switch (op) {
-    case FNT_RS_OP_ENCODE: return ws_bytes(p, W, enc_nbuf_max(p));
+    case FNT_RS_OP_ENCODE:
+      return ws_bytes(p, W, enc_nbuf_max(p)) +
+             (p->n_out < p->n ? align256((size_t)p->n * W * 4) : 0);
+    case FNT_RS_OP_ENCODE_SYS:
+    case FNT_RS_OP_DECODE_SYS: return sys_workspace_bytes(p, W);
     case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf_max(p));
     case FNT_RS_OP_FNT: return ws_bytes(p, W, fnt_nbuf(p));
     case FNT_RS_OP_ENCODE_HOST: {
-      const size_t stage = ((size_t)p->k * W * 2 + 255) / 256 * 256 + (size_t)p->n * W * 4;
-      return stage + ws_bytes(p, W, enc_nbuf_max(p));
+      const size_t stage = align256((size_t)p->k * W * 2) + align256((size_t)p->n_out * W * 4);
+      return stage + fnt_rs_workspace_bytes(p, W, FNT_RS_OP_ENCODE);
     }
     case FNT_RS_OP_DECODE_HOST: {
       const size_t stage = ((size_t)p->k * W * 4 + 255) / 256 * 256 + ((size_t)p->k * W * 2 + 255) / 256 * 256;
@@ -1048,15 +1065,25 @@ size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
   }
 }
 
-static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
 
 int fnt_rs_encode(fnt_rs_plan p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
                   size_t W, void* workspace, void* stream) {
   if (!p || W == 0) return W == 0 && p ? FNT_RS_OK : FNT_RS_E_ARG;
   if (!src || !enc || ld_src < W || ld_enc < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(src, 2) || !aligned(enc, 4)) return FNT_RS_E_ARG;
-  if (ws_bytes(p, W, enc_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
-  return do_encode(p, src, ld_src, enc, ld_enc, W, workspace, S(stream));
+  if (p->n_out == p->n) {
+    if (ws_bytes(p, W, enc_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+    return do_encode(p, src, ld_src, enc, ld_enc, W, workspace, S(stream));
+  }
+  // punctured code: all n rows into the workspace, the first n_out kept
+  if (!workspace) return FNT_RS_E_WORKSPACE;
+  uint32_t* full = static_cast<uint32_t*>(workspace);
+  void* rest = static_cast<uint8_t*>(workspace) + align256((size_t)p->n * W * 4);
+  int rc = do_encode(p, src, ld_src, full, W, W, rest, S(stream));
+  if (rc) return rc;
+  return cuda_ok(cudaMemcpy2DAsync(enc, ld_enc * 4, full, W * 4, W * 4, p->n_out,
+                                   cudaMemcpyDeviceToDevice, S(stream)));
 }
 
 int fnt_rs_decode_prepare(fnt_rs_plan p, const uint32_t* positions, uint32_t npos, void* stream) {
@@ -1095,7 +1122,7 @@ int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
 
 int fnt_rs_decode_full(fnt_rs_plan p, const uint32_t* enc, size_t ld_enc, uint16_t* out,
                        size_t ld_out, size_t W, void* workspace, void* stream) {
-  if (!p) return FNT_RS_E_ARG;
+  if (!p || p->n_out < p->n) return FNT_RS_E_ARG;  // a punctured codeword is never complete
   if (W == 0) return FNT_RS_OK;
   if (!enc || !out || ld_enc < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(enc, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
@@ -1148,6 +1175,34 @@ int fnt_rs_decode_full(fnt_rs_plan p, const uint32_t* enc, size_t ld_enc, uint16
   return cuda_ok(cudaGetLastError());
 }
 
+}  // extern "C"
+
+namespace fntrs {
+
+size_t fnt_columns_work_bytes(const fnt_rs_plan_s* p, size_t W) {
+  if (p->n <= (uint32_t)kTileMaxL || W == 0) return 0;
+  return (size_t)p->n * std::min(W, split_chunk(p->n, 1)) * 4;
+}
+
+int fnt_columns(fnt_rs_plan_s* p, const uint32_t* in, size_t ld_in, uint32_t* out,
+                size_t ld_out, size_t W, bool inverse, void* work, cudaStream_t st) {
+  if (p->n <= (uint32_t)kTileMaxL)
+    return run_fnt_default((int)p->n, in, ld_in, out, ld_out, (int)W, inverse, p->uinv, nullptr,
+                           st);
+  const size_t wc = split_chunk(p->n, 1);
+  for (size_t c0 = 0; c0 < W; c0 += wc) {
+    const int w = (int)std::min(wc, W - c0);
+    int rc = run_fnt_default((int)p->n, in + c0, ld_in, out + c0, ld_out, w, inverse, p->uinv,
+                             static_cast<uint32_t*>(work), st);
+    if (rc) return rc;
+  }
+  return FNT_RS_OK;
+}
+
+}  // namespace fntrs
+
+extern "C" {
+
 int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, size_t ld_out,
                size_t W, int inverse, void* workspace, void* stream) {
   if (!p) return FNT_RS_E_ARG;
@@ -1155,17 +1210,7 @@ int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, s
   if (!in || !out || ld_in < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(in, 4) || !aligned(out, 4)) return FNT_RS_E_ARG;
   if (ws_bytes(p, W, fnt_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
-  if (!p->split)
-    return run_fnt_default((int)p->n, in, ld_in, out, ld_out, (int)W, inverse != 0, p->uinv,
-                           nullptr, S(stream));
-  const size_t wc = split_chunk(p->n, 1);
-  for (size_t c0 = 0; c0 < W; c0 += wc) {
-    const int w = (int)std::min(wc, W - c0);
-    int rc = run_fnt_default((int)p->n, in + c0, ld_in, out + c0, ld_out, w, inverse != 0,
-                             p->uinv, static_cast<uint32_t*>(workspace), S(stream));
-    if (rc) return rc;
-  }
-  return FNT_RS_OK;
+  return fnt_columns(p, in, ld_in, out, ld_out, W, inverse != 0, workspace, S(stream));
 }
 
 int fnt_rs_encode_host(fnt_rs_plan p, const uint16_t* h_src, uint32_t* h_enc, size_t W,
@@ -1175,12 +1220,13 @@ int fnt_rs_encode_host(fnt_rs_plan p, const uint16_t* h_src, uint32_t* h_enc, si
   cudaStream_t st = S(stream);
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   uint16_t* d_src = reinterpret_cast<uint16_t*>(ws);
-  uint32_t* d_enc = reinterpret_cast<uint32_t*>(ws + ((size_t)p->k * W * 2 + 255) / 256 * 256);
-  void* rest = reinterpret_cast<uint8_t*>(d_enc) + (size_t)p->n * W * 4;
+  uint32_t* d_enc = reinterpret_cast<uint32_t*>(ws + align256((size_t)p->k * W * 2));
+  void* rest = reinterpret_cast<uint8_t*>(d_enc) + align256((size_t)p->n_out * W * 4);
   int rc = cuda_ok(cudaMemcpyAsync(d_src, h_src, (size_t)p->k * W * 2, cudaMemcpyHostToDevice, st));
   if (rc) return rc;
   if ((rc = fnt_rs_encode(p, d_src, W, d_enc, W, W, rest, stream))) return rc;
-  if ((rc = cuda_ok(cudaMemcpyAsync(h_enc, d_enc, (size_t)p->n * W * 4, cudaMemcpyDeviceToHost, st))))
+  if ((rc = cuda_ok(cudaMemcpyAsync(h_enc, d_enc, (size_t)p->n_out * W * 4,
+                                    cudaMemcpyDeviceToHost, st))))
     return rc;
   return cuda_ok(cudaStreamSynchronize(st));
 }
