@@ -293,6 +293,52 @@ def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30, patterns_per_s
                        f"per shape), first {len(trace)} requests; inputs generated on the device")}
 
 
+def systematic_measure(pkg, dev, reps=20):
+    """Systematic code on the headline shape: encode, decode with erasures, decode with
+    every source position received (the direct path)."""
+    import torch
+
+    cfg = WORKLOAD
+    n, k, W = cfg.n, cfg.k, cfg.W
+    plan = pkg.Plan(n, k, device=dev)
+    src = pkg.to_device(cfg.source(), dev)
+    enc = plan.encode_sys(src)
+    pos = cfg.positions()
+    recv = torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
+    direct = np.arange(k, dtype=np.uint32)
+    recv_d = enc[:k].contiguous()
+    out = torch.empty((k, W), dtype=torch.int16, device=dev)
+    ws_e = plan.workspace(W, pkg.OP_ENCODE_SYS)
+    ws_d = plan.workspace(W, pkg.OP_DECODE_SYS)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_e = timed(lambda: pkg.fnt_rs_encode_sys(plan.handle, src, enc, ws_e))
+    t_d = timed(lambda: pkg.fnt_rs_decode_sys(plan.handle, recv, pos, out, ws_d))
+    ok = np.array_equal(pkg.to_host(out), cfg.source())
+    t_dd = timed(lambda: pkg.fnt_rs_decode_sys(plan.handle, recv_d, direct, out, ws_d))
+    ok = ok and np.array_equal(pkg.to_host(out), cfg.source()) and plan.status() == 0
+    gb = k * W * 2 / 1e9
+    return {"encode_sys_ms": t_e, "decode_sys_ms": t_d, "decode_sys_direct_ms": t_dd,
+            "encode_sys_gbs": gb / (t_e * 1e-3), "decode_sys_gbs": gb / (t_d * 1e-3),
+            "decode_sys_direct_gbs": gb / (t_dd * 1e-3), "round_trip_ok": bool(ok),
+            "config": f"{cfg.name}, systematic code; decode with the step's erasure pattern "
+                      "(pattern cached) and with positions 0..k-1 received; L2 flushed"}
+
+
 def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
     """The cfg5 arrival rates, each on the head of its seeded trace, plus a
     fresh-pattern variant (every decode request brings a new erasure pattern)."""
@@ -550,6 +596,7 @@ def run_gpu(args):
     if world == 1 and not args.no_extras:
         line["ragged"] = ragged_measure(pkg, dev)
         line["serving"] = serving_sweep(pkg, count=args.serving_requests)
+        line["systematic"] = systematic_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
