@@ -339,6 +339,63 @@ def systematic_measure(pkg, dev, reps=20):
                       "(pattern cached) and with positions 0..k-1 received; L2 flushed"}
 
 
+def wire_measure(pkg, dev, reps=20):
+    """16-bit wire format on the headline shape: device encode to 16-bit symbols +
+    escapes, and decode from them (pattern cached), against the 32-bit calls."""
+    import torch
+
+    cfg = WORKLOAD
+    n, k, W = cfg.n, cfg.k, cfg.W
+    plan = pkg.Plan(n, k, device=dev)
+    src = pkg.to_device(cfg.source(), dev)
+    enc16 = torch.empty((n, W), dtype=torch.int16, device=dev)
+    enc32 = torch.empty((n, W), dtype=torch.int32, device=dev)
+    cap = pkg.fnt_rs_wire_escape_cap(plan.handle, W)
+    esc = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws_e = plan.workspace(W, pkg.OP_ENCODE_WIRE)
+    ws_e32 = plan.workspace(W, pkg.OP_ENCODE)
+    pkg.fnt_rs_encode_wire(plan.handle, src, enc16, esc, cnt, ws_e)
+    m = int(cnt.item())
+    pos = cfg.positions()
+    rank_of = torch.full((n,), -1, dtype=torch.int64, device=dev)
+    pos_d = torch.from_numpy(pos.astype(np.int64)).to(dev)
+    rank_of[pos_d] = torch.arange(len(pos), device=dev)
+    e = esc[:m].to(torch.int64)
+    keep = rank_of[e[:, 0]] >= 0
+    r_esc = torch.stack([rank_of[e[keep, 0]], e[keep, 1]], 1).to(torch.int32).contiguous()
+    recv16 = torch.index_select(enc16, 0, pos_d)
+    out = torch.empty((k, W), dtype=torch.int16, device=dev)
+    ws_d = plan.workspace(W, pkg.OP_DECODE_WIRE)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_e = timed(lambda: pkg.fnt_rs_encode_wire(plan.handle, src, enc16, esc, cnt, ws_e))
+    t_e32 = timed(lambda: pkg.fnt_rs_encode(plan.handle, src, enc32, ws_e32))
+    t_d = timed(lambda: pkg.fnt_rs_decode_wire(plan.handle, recv16, pos, r_esc, len(r_esc), out,
+                                               ws_d))
+    ok = np.array_equal(pkg.to_host(out), cfg.source()) and plan.status() == 0
+    gb = k * W * 2 / 1e9
+    return {"encode_wire_ms": t_e, "encode_u32_ms": t_e32, "decode_wire_ms": t_d,
+            "encode_wire_gbs": gb / (t_e * 1e-3), "decode_wire_gbs": gb / (t_d * 1e-3),
+            "escapes": m, "escapes_in_received_rows": int(len(r_esc)), "round_trip_ok": bool(ok),
+            "config": f"{cfg.name}; 16-bit symbols + escape list; decode with the step's "
+                      "erasure pattern (cached); L2 flushed"}
+
+
 def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
     """The cfg5 arrival rates, each on the head of its seeded trace, plus a
     fresh-pattern variant (every decode request brings a new erasure pattern)."""
@@ -558,10 +615,45 @@ def run_gpu(args):
         pkg.fnt_rs_decode_host(plan.handle, h_recv, pos0, h_out, ws_dh, stream)
         e2e_times.append(time.perf_counter() - t0)
     assert np.array_equal(h_out.numpy().view(np.uint16), cfg.source())
+    e2e_u32_ms = statistics.median(e2e_times) * 1e3
+    e2e_u32 = {"value": world * src_bytes / (e2e_u32_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": k * W * 2 + k * W * 4,
+               "d2h_bytes_per_step": n * W * 4 + k * W * 2,
+               "format": "32-bit symbols (fnt_rs_encode_host / fnt_rs_decode_host)"}
+
+    # the same round trip in the 16-bit wire format (symbols as 16 bits, the
+    # value 65536 as escapes): the public host-buffer calls a sender and a
+    # receiver make
+    h_enc16 = torch.empty((n, W), dtype=torch.int16).pin_memory()
+    h_esc = np.zeros((pkg.fnt_rs_wire_escape_cap(plan.handle, W), 2), dtype=np.uint32)
+    ws_ew = plan.workspace(W, pkg.OP_ENCODE_WIRE_HOST)
+    ws_dw = torch.empty(pkg.fnt_rs_workspace_bytes(plan.handle, W, pkg.OP_DECODE_WIRE_HOST),
+                        dtype=torch.uint8, device=dev)
+    nesc = pkg.fnt_rs_encode_wire_host(plan.handle, h_src, h_enc16, h_esc, ws_ew, stream)
+    sym16 = h_enc16.numpy().view(np.uint16)
+    h_recv16 = torch.from_numpy(np.ascontiguousarray(sym16[pos0]).view(np.int16)).pin_memory()
+    r_esc = np.ascontiguousarray(h_esc[:nesc][np.isin(h_esc[:nesc, 0], pos0)])
+    rank_of = np.full(n, -1, np.int64)
+    rank_of[pos0] = np.arange(len(pos0))
+    r_esc[:, 0] = rank_of[r_esc[:, 0]]  # packet -> index of the received row
+    e2e_times, e2e_enc = [], []
+    for i in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = pkg.fnt_rs_encode_wire_host(plan.handle, h_src, h_enc16, h_esc, ws_ew, stream)
+        t1 = time.perf_counter()
+        pkg.fnt_rs_decode_wire_host(plan.handle, h_recv16, pos0, r_esc, h_out, ws_dw, stream)
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_enc.append(t1 - t0)
+    assert m == nesc and np.array_equal(h_out.numpy().view(np.uint16), cfg.source())
     e2e_ms = statistics.median(e2e_times) * 1e3
+    e2e_enc_ms = statistics.median(e2e_enc) * 1e3
     e2e = {"value": world * src_bytes / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": k * W * 2 + k * W * 4,
-           "d2h_bytes_per_step": n * W * 4 + k * W * 2}
+           "h2d_bytes_per_step": k * W * 2 + k * W * 2 + len(r_esc) * 8,
+           "d2h_bytes_per_step": n * W * 2 + 4 + nesc * 8 + k * W * 2,
+           "format": "16-bit wire symbols + escape list (fnt_rs_encode_wire_host / "
+                     "fnt_rs_decode_wire_host)",
+           "escapes": int(nesc), "ms": e2e_ms, "encode_call_ms": e2e_enc_ms}
 
     if rank != 0:
         return
@@ -589,6 +681,7 @@ def run_gpu(args):
                              "frac": achieved_gbs / hbm_peak, "peak_source": peak_src,
                              "bytes_per_launch": dom_bytes}},
         "e2e": e2e,
+        "e2e_u32": e2e_u32,
         "gpu_launches": int(launches),
         "wall_ms_per_step": t_wall * 1e3 / args.steps,
         "clocks": clk.summary(),
@@ -597,6 +690,7 @@ def run_gpu(args):
         line["ragged"] = ragged_measure(pkg, dev)
         line["serving"] = serving_sweep(pkg, count=args.serving_requests)
         line["systematic"] = systematic_measure(pkg, dev)
+        line["wire"] = wire_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -73,7 +73,11 @@ enum fnt_rs_op {
   FNT_RS_OP_ENCODE_HOST = 3,    /* fnt_rs_encode_host staging */
   FNT_RS_OP_DECODE_HOST = 4,    /* fnt_rs_decode_host staging */
   FNT_RS_OP_ENCODE_SYS = 5,     /* fnt_rs_encode_sys */
-  FNT_RS_OP_DECODE_SYS = 6      /* fnt_rs_decode_sys */
+  FNT_RS_OP_DECODE_SYS = 6,     /* fnt_rs_decode_sys */
+  FNT_RS_OP_ENCODE_WIRE = 7,    /* fnt_rs_encode_wire */
+  FNT_RS_OP_DECODE_WIRE = 8,    /* fnt_rs_decode_wire */
+  FNT_RS_OP_ENCODE_WIRE_HOST = 9,   /* fnt_rs_encode_wire_host staging */
+  FNT_RS_OP_DECODE_WIRE_HOST = 10   /* fnt_rs_decode_wire_host staging */
 };
 
 typedef struct fnt_rs_plan_s* fnt_rs_plan;
@@ -293,6 +297,72 @@ int fnt_rs_encode_sys(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint
 int fnt_rs_decode_sys(fnt_rs_plan plan, const uint32_t* recv, size_t ld_recv,
                       const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
                       size_t W, void* workspace, void* stream);
+
+/*
+ * 16-bit wire format (Sec. II.B, "Design of the code on GF(65537)": every
+ * symbol but 65536 fits in 16 bits; the positions that hold 65536 are sent
+ * beside the packets, in their headers).  A symbol travels as its low 16
+ * bits (65536 as 0) and every symbol equal to 65536 is listed as an escape
+ * {row, col}: row = packet (encoded row, or index of a received row), col =
+ * codeword.  On random data one symbol in 65537 is an escape.
+ */
+typedef struct fnt_rs_escape_s {
+  uint32_t row, col;
+} fnt_rs_escape;
+
+/*
+ * Encode to the wire format: the symbols of fnt_rs_encode, as 16 bits, into
+ * enc [n_out][ld_enc] uint16 (device), and their escapes into esc (device,
+ * esc_cap entries, in no particular order; each escaped symbol listed once).
+ * *esc_count (device word) receives the number of escapes, also when it
+ * exceeds esc_cap: the entries beyond esc_cap are then dropped (the symbols
+ * are still complete) and the call can be repeated with a larger array.
+ * fnt_rs_wire_escape_cap() is a capacity that random data never exceeds in
+ * practice (about 1/64 of the symbols; the expected share is 1/65537); an
+ * adversarial source can make up to k - 1 symbols of a codeword escapes.
+ * workspace: fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_ENCODE_WIRE) bytes (a
+ * punctured code needs no extra rows: rows >= n_out are never stored).
+ * esc must be 8-byte aligned, esc_count 4-byte aligned.  Enqueued on `stream`.
+ */
+size_t fnt_rs_wire_escape_cap(fnt_rs_plan plan, size_t W);
+int fnt_rs_encode_wire(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint16_t* enc,
+                       size_t ld_enc, size_t W, fnt_rs_escape* esc, uint32_t esc_cap,
+                       uint32_t* esc_count, void* workspace, void* stream);
+
+/*
+ * Decode from the wire format: recv [npos][ld_recv] uint16 (device, row i =
+ * the packet received at positions[i]) and its escapes esc (device, nesc
+ * entries, row = index of the received row, any order); otherwise as
+ * fnt_rs_decode.  Escapes of rows >= k (not used by the decode) are skipped;
+ * an escape outside the received rows or columns, or whose 16-bit symbol is
+ * not 0, is not valid wire data: it raises FNT_RS_E_RANGE in the status word
+ * (and the decoded words are then unspecified).  workspace:
+ * fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_DECODE_WIRE) bytes (the k rows
+ * are widened to 32 bits there).  Enqueued on `stream`.
+ */
+int fnt_rs_decode_wire(fnt_rs_plan plan, const uint16_t* recv, size_t ld_recv,
+                       const uint32_t* positions, uint32_t npos, const fnt_rs_escape* esc,
+                       uint32_t nesc, uint16_t* out, size_t ld_out, size_t W, void* workspace,
+                       void* stream);
+
+/*
+ * Host-buffer variants of the wire calls (dense host buffers, ld = W; the
+ * copies, the kernels and the escape handling are enqueued on `stream`,
+ * which the call synchronises).  Encode: h_enc [n_out][W] uint16; the
+ * escapes are written to h_esc sorted by row, then column, and their number
+ * to *nesc.  Returns FNT_RS_E_ARG if they do not fit in esc_cap (*nesc then
+ * says how many there are) and FNT_RS_E_WORKSPACE if they exceed
+ * fnt_rs_wire_escape_cap(plan, W), the number the workspace stages (use
+ * fnt_rs_encode_wire with a larger array).  Decode: h_recv [npos][W] uint16,
+ * only its first k rows are copied; h_esc: nesc escapes (host).  workspace:
+ * FNT_RS_OP_ENCODE_WIRE_HOST / FNT_RS_OP_DECODE_WIRE_HOST bytes.
+ */
+int fnt_rs_encode_wire_host(fnt_rs_plan plan, const uint16_t* h_src, uint16_t* h_enc, size_t W,
+                            fnt_rs_escape* h_esc, uint32_t esc_cap, uint32_t* nesc,
+                            void* workspace, void* stream);
+int fnt_rs_decode_wire_host(fnt_rs_plan plan, const uint16_t* h_recv, const uint32_t* positions,
+                            uint32_t npos, const fnt_rs_escape* h_esc, uint32_t nesc,
+                            uint16_t* h_out, size_t W, void* workspace, void* stream);
 
 /*
  * Reads the plan's device status word (synchronising `stream`), clears it and

@@ -24,6 +24,7 @@ from ._lib import FntRsError, Group, LIB_PATH, Request, load  # noqa: F401
 P = 65537
 OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
 OP_ENCODE_SYS, OP_DECODE_SYS = 5, 6
+OP_ENCODE_WIRE, OP_DECODE_WIRE, OP_ENCODE_WIRE_HOST, OP_DECODE_WIRE_HOST = 7, 8, 9, 10
 SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT, SCHED_CPA = 0, 1, 2, 3, 4
 SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split", SCHED_CPA: "cpa"}
 
@@ -330,6 +331,66 @@ def fnt_rs_decode_sys(plan, recv: torch.Tensor, positions, out: torch.Tensor, wo
            "fnt_rs_decode_sys")
 
 
+def fnt_rs_wire_escape_cap(plan, W: int) -> int:
+    return int(load().fnt_rs_wire_escape_cap(plan, W))
+
+
+def fnt_rs_encode_wire(plan, src: torch.Tensor, enc: torch.Tensor, esc: torch.Tensor,
+                       esc_count: torch.Tensor, workspace=None, stream=None):
+    """16-bit wire encode: enc [n_out][W] 16-bit, esc [cap][2] 32-bit {row, col} pairs
+    (unordered), esc_count one 32-bit device word (may exceed cap)."""
+    W, ld_src = _cols(src)
+    W2, ld_enc = _cols(enc)
+    if W2 != W:
+        raise ValueError("src and enc must have the same number of columns")
+    if esc.dim() != 2 or esc.shape[1] != 2 or not esc.is_contiguous():
+        raise ValueError("esc must be a contiguous [cap][2] tensor")
+    _check(load().fnt_rs_encode_wire(plan, _ptr(src), ld_src, _ptr(enc), ld_enc, W, _ptr(esc),
+                                     esc.shape[0], _ptr(esc_count), _ptr(workspace),
+                                     _stream(stream)), "fnt_rs_encode_wire")
+
+
+def fnt_rs_decode_wire(plan, recv: torch.Tensor, positions, esc: torch.Tensor, nesc: int,
+                       out: torch.Tensor, workspace=None, stream=None):
+    """16-bit wire decode: recv [npos][W] 16-bit, esc [>= nesc][2] device {row, col} pairs."""
+    W, ld_recv = _cols(recv)
+    W2, ld_out = _cols(out)
+    if W2 != W:
+        raise ValueError("recv and out must have the same number of columns")
+    if esc is not None and (esc.dim() != 2 or esc.shape[1] != 2 or not esc.is_contiguous()
+                            or esc.shape[0] < nesc):
+        raise ValueError("esc must be a contiguous [>= nesc][2] tensor")
+    pos = _positions(positions)
+    _check(load().fnt_rs_decode_wire(plan, _ptr(recv), ld_recv, pos.ctypes.data, len(pos),
+                                     _ptr(esc), nesc, _ptr(out), ld_out, W, _ptr(workspace),
+                                     _stream(stream)), "fnt_rs_decode_wire")
+
+
+def fnt_rs_encode_wire_host(plan, h_src: torch.Tensor, h_enc: torch.Tensor, h_esc: np.ndarray,
+                            workspace, stream=None) -> int:
+    """Host-buffer wire encode; returns the number of escapes written (sorted) to h_esc."""
+    W = h_src.shape[1]
+    if h_esc.dtype != np.uint32 or h_esc.ndim != 2 or h_esc.shape[1] != 2 or \
+            not h_esc.flags.c_contiguous:
+        raise ValueError("h_esc must be a C-contiguous uint32 [cap][2] array")
+    cnt = ctypes.c_uint32(0)
+    _check(load().fnt_rs_encode_wire_host(plan, _ptr(h_src), _ptr(h_enc), W, h_esc.ctypes.data,
+                                          h_esc.shape[0], ctypes.byref(cnt), _ptr(workspace),
+                                          _stream(stream)), "fnt_rs_encode_wire_host")
+    return cnt.value
+
+
+def fnt_rs_decode_wire_host(plan, h_recv: torch.Tensor, positions, h_esc: np.ndarray,
+                            h_out: torch.Tensor, workspace, stream=None):
+    W = h_recv.shape[1]
+    pos = _positions(positions)
+    h_esc = np.ascontiguousarray(np.asarray(h_esc, dtype=np.uint32).reshape(-1, 2))
+    _check(load().fnt_rs_decode_wire_host(plan, _ptr(h_recv), pos.ctypes.data, len(pos),
+                                          h_esc.ctypes.data, len(h_esc), _ptr(h_out), W,
+                                          _ptr(workspace), _stream(stream)),
+           "fnt_rs_decode_wire_host")
+
+
 def fnt_rs_set_schedule(plan, op: int, sched: int) -> None:
     _check(load().fnt_rs_set_schedule(plan, op, sched), "fnt_rs_set_schedule")
 
@@ -464,6 +525,39 @@ class Plan:
             out = torch.empty((self.k, W), dtype=torch.int16, device=recv.device)
         fnt_rs_decode_sys(self.handle, recv, positions, out, self.workspace(W, OP_DECODE_SYS),
                           stream)
+        return out
+
+    def encode_wire(self, src: torch.Tensor, cap: int = 0, stream=None):
+        """(symbols [n_out][W] 16-bit, escapes [m][2] {row, col} sorted) on the device.
+
+        Reads the escape count back (synchronising the stream); a count above
+        the capacity re-runs the encode with room for all of them.
+        """
+        W = src.shape[1]
+        rows = getattr(self, "n_out", self.n)
+        enc = torch.empty((rows, W), dtype=torch.int16, device=src.device)
+        cap = cap or fnt_rs_wire_escape_cap(self.handle, W)
+        cnt = torch.zeros(1, dtype=torch.int32, device=src.device)
+        while True:
+            esc = torch.empty((cap, 2), dtype=torch.int32, device=src.device)
+            fnt_rs_encode_wire(self.handle, src, enc, esc, cnt,
+                               self.workspace(W, OP_ENCODE_WIRE), stream)
+            m = int(cnt.item())
+            if m <= cap:
+                break
+            cap = m
+        e = esc[:m].to(torch.int64)
+        order = torch.argsort(e[:, 0] * (1 << 32) + e[:, 1])
+        return enc, esc[:m][order].contiguous()
+
+    def decode_wire(self, recv: torch.Tensor, positions, esc: torch.Tensor, out=None,
+                    stream=None):
+        W = recv.shape[1]
+        if out is None:
+            out = torch.empty((self.k, W), dtype=torch.int16, device=recv.device)
+        nesc = 0 if esc is None else esc.shape[0]
+        fnt_rs_decode_wire(self.handle, recv, positions, esc, nesc, out,
+                           self.workspace(W, OP_DECODE_WIRE), stream)
         return out
 
     def autotune(self, W: int, op: int, stream=None) -> list:

@@ -59,6 +59,12 @@ def load(build_if_missing: bool = False):
             "fnt_rs_plan_set_length": (i32, [vp, u32]),
             "fnt_rs_encode_sys": (i32, [vp, vp, sz, vp, sz, sz, vp, vp]),
             "fnt_rs_decode_sys": (i32, [vp, vp, sz, vp, u32, vp, sz, sz, vp, vp]),
+            "fnt_rs_wire_escape_cap": (sz, [vp, sz]),
+            "fnt_rs_encode_wire": (i32, [vp, vp, sz, vp, sz, sz, vp, u32, vp, vp, vp]),
+            "fnt_rs_decode_wire": (i32, [vp, vp, sz, vp, u32, vp, u32, vp, sz, sz, vp, vp]),
+            "fnt_rs_encode_wire_host": (i32, [vp, vp, vp, sz, vp, u32, ctypes.POINTER(u32),
+                                              vp, vp]),
+            "fnt_rs_decode_wire_host": (i32, [vp, vp, vp, u32, vp, u32, vp, sz, vp, vp]),
             "fnt_rs_set_schedule": (i32, [vp, i32, i32]),
             "fnt_rs_get_schedule": (i32, [vp, i32]),
             "fnt_rs_autotune": (i32, [vp, sz, i32, vp, i32, vp]),

@@ -22,7 +22,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-Xptxas", "-warn-spills"]
 SOURCES = ["plan.cu", "pattern.cu", "inst_small.cu", "inst_mid.cu", "inst_big.cu",
            "inst_huge.cu", "inst_split.cu", "noalloc.cu", "ragged.cu", "ragged_kernel.cu", "server.cu",
-           "systematic.cu"]
+           "systematic.cu", "wire.cu",
+           "hostpipe.cu"]
 
 
 def nvcc() -> str:

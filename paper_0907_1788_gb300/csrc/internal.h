@@ -41,6 +41,19 @@ struct PatternSlot {
 int alloc_pattern_tables(PatternSlot& sl, size_t n, bool staging);
 void free_pattern_tables(PatternSlot& sl);
 
+// Streams and events of the host-buffer entry points, which overlap the
+// host-to-device copies, the kernels and the device-to-host copies of
+// successive column chunks (hostpipe.cu).
+constexpr int kPipeChunks = 8;
+struct HostPipe {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, out_done = nullptr;
+  cudaEvent_t in_done[kPipeChunks] = {};
+  cudaEvent_t comp_done[kPipeChunks] = {};
+};
+int pipe_init(HostPipe& h);
+void pipe_free(HostPipe& h);
+
 constexpr int kPatternSlots = 4;
 constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
 
@@ -77,6 +90,7 @@ struct fnt_rs_plan_s {
   uint32_t n_out = 0;         // code length after puncturing (k <= n_out <= n)
   fntrs::PatternSlot sys;     // pattern of positions 0..k-1 (systematic code), built on first use
   bool sys_ready = false;
+  fntrs::HostPipe pipe;       // host-buffer entry points
 };
 
 namespace fntrs {
@@ -96,6 +110,10 @@ size_t ws_bytes(const fnt_rs_plan_s* p, size_t W, int nbuf);
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // workspace of the systematic encode / decode (systematic.cu)
 size_t sys_workspace_bytes(const fnt_rs_plan_s* p, size_t W);
+// workspace of the 16-bit wire-format device calls (wire.cu) and of the
+// host-buffer calls (hostpipe.cu)
+size_t wire_workspace_bytes(const fnt_rs_plan_s* p, size_t W, int op);
+size_t host_workspace_bytes(fnt_rs_plan_s* p, size_t W, int op);
 int get_tables(int L, Tables* out);
 uint32_t hinv(uint32_t a);
 int validate_positions(const fnt_rs_plan_s* p, const uint32_t* pos, uint32_t npos);
@@ -114,12 +132,35 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st,
 bool fused_plan_applies(const fnt_rs_plan_s* p);
 size_t pattern_scratch_words(uint32_t n, uint32_t k);
 int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st);
+// 16-bit wire output of an encode (see KArgs::wire): symbols to enc as u16,
+// escapes of the value 65536 to esc (count on the device), rows < rows kept.
+struct WireSpec {
+  uint16_t* enc;
+  size_t ld;
+  uint2* esc;
+  uint32_t* count;
+  uint32_t cap;
+  uint32_t rows;
+  uint32_t col0;  // column of enc[.][0] in the escapes' numbering
+};
+// Widens rows [0, k) x columns [0, W) of 16-bit received symbols to u32 (dst,
+// ld_dst) and writes 65536 at the escapes that fall in columns [c_lo, c_hi)
+// of rows < k (escape columns are absolute: dst column = escape column).
+int wire_widen(fnt_rs_plan_s* p, const uint16_t* recv, size_t ld_recv, uint32_t* dst,
+               size_t ld_dst, size_t W, cudaStream_t st);
+int wire_escapes(fnt_rs_plan_s* p, const uint2* esc, uint32_t nesc, uint32_t nrecv,
+                 uint32_t* dst, size_t ld_dst, size_t W, size_t c_lo, size_t c_hi,
+                 cudaStream_t st);
+constexpr uint32_t kEscStage = 65536;  // escapes staged at once by the host decode
+
 // Encode of n > 8192 in two passes (radix-n/4096 cross pass, 4096-point
 // local transforms) through `work` of ws_bytes(p, W, enc_nbuf(p)) bytes.
+// With `wire` the output goes there instead of enc (which may be null).
 int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                       size_t ld_enc, size_t W, uint32_t* work, cudaStream_t st);
+                       size_t ld_enc, size_t W, uint32_t* work, cudaStream_t st,
+                       const WireSpec* wire = nullptr);
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc, size_t ld_enc,
-              size_t W, void* workspace, cudaStream_t st);
+              size_t W, void* workspace, cudaStream_t st, const WireSpec* wire = nullptr);
 // decode with explicit pattern tables (slots != 0: row z of recv is position z);
 // with out32 the coefficients go there as u32 (ld_out) and `out` is unused
 int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,

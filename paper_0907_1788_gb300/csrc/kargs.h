@@ -61,6 +61,16 @@ struct KArgs {
   int slots = 0;      // decode input indexed by position (row z = position z)
   int deg_child = 0;  // product-tree level: degree of the child polynomials
   int nodes = 0;      // product-tree level: number of child nodes
+  // 16-bit wire output of an encode (wire != 0): `out` is u16, a symbol is
+  // stored as its low 16 bits and every symbol equal to 65536 is appended to
+  // esc as {row, col_base + column} (*esc_count counts all of them, entries
+  // beyond esc_cap are dropped); rows >= wire_rows are not stored.
+  int wire = 0;
+  int wire_rows = 0;
+  int col_base = 0;
+  uint32_t esc_cap = 0;
+  uint2* esc = nullptr;
+  uint32_t* esc_count = nullptr;
 };
 
 // Arguments of the one-launch log-domain pattern build (n <= tile limit).

@@ -116,6 +116,33 @@ struct LoadRecv {
 // Storers: spectrum index j of tile codeword c.
 // ---------------------------------------------------------------------------
 
+// 16-bit wire output (Sec. II.B: every symbol but 65536 fits 16 bits; the
+// positions of 65536 travel separately): the low 16 bits of v in [0, p) go
+// to row `row`, column `col` of the u16 matrix, and a 65536 is listed in the
+// escape array.  The escape is rare (one symbol in 65537 on random data), so
+// the atomic is off the common path.
+struct WireOut {
+  uint16_t* out;
+  size_t ld;
+  uint2* esc;
+  uint32_t* count;
+  uint32_t cap;
+  int rows, col_base;
+  static __device__ __forceinline__ WireOut make(const KArgs& a) {
+    return WireOut{static_cast<uint16_t*>(a.out), a.ld_out, a.esc, a.esc_count, a.esc_cap,
+                   a.wire_rows, a.col_base};
+  }
+  __device__ __forceinline__ void escape(uint32_t row, int col) const {
+    const uint32_t i = atomicAdd(count, 1u);
+    if (i < cap) esc[i] = make_uint2(row, (uint32_t)(col_base + col));
+  }
+  __device__ __forceinline__ void put(uint32_t row, int col, uint32_t v) const {
+    if (row >= (uint32_t)rows) return;
+    out[(size_t)row * ld + col] = (uint16_t)v;
+    if (v == 65536u) escape(row, col);
+  }
+};
+
 // out row = cc + C*j, value reduced to [0, p) and optionally scaled.
 template <int WT>
 struct StoreRows32 {
@@ -123,9 +150,11 @@ struct StoreRows32 {
   size_t ld;
   int col0, W, C, cc;
   uint32_t scale, rmul, nmask;
+  int wire;
+  WireOut wo;
   static __device__ __forceinline__ StoreRows32 make(const KArgs& a, int tx, int ty) {
     return StoreRows32{static_cast<uint32_t*>(a.out), a.ld_out, tx * WT, a.W, a.C, ty, a.scale,
-                       a.row_mul, (uint32_t)a.n - 1u};
+                       a.row_mul, (uint32_t)a.n - 1u, a.wire, WireOut::make(a)};
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) const {
     const int col = col0 + c;
@@ -133,7 +162,10 @@ struct StoreRows32 {
     if (scale != 1u) v = m_mul(v, scale);
     uint32_t row = (uint32_t)(cc + C * j);
     if (rmul != 1u) row = (rmul * row) & nmask;
-    out[(size_t)row * ld + col] = m_to_p(v);
+    if (wire)
+      wo.put(row, col, m_to_p(v));
+    else
+      out[(size_t)row * ld + col] = m_to_p(v);
   }
 };
 
@@ -163,7 +195,10 @@ struct StoreLocal {
       if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
       const size_t orow =
           a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
-      static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
+      if (MODE == LM_ENC && a.wire)
+        WireOut::make(a).put((uint32_t)orow, col, m_to_p(v));
+      else
+        static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
     } else if constexpr (MODE == LM_WORK) {
       if ((int)row < a.out_limit) static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
     } else if constexpr (MODE == LM_WORK_AHAT) {
@@ -367,10 +402,29 @@ __global__ void __launch_bounds__(NT, 1)
           dft_reg<RL, false>(x);
           const int col = col0 + c;
           if (col < a.W) {
-            uint32_t* o = out + (size_t)(cc + C * S::natural(b * RL)) * ld + col;
-            const size_t step = (size_t)C * (S::L / RL) * ld;
+            if (a.wire) {
+              // 16-bit symbols: same addressing as below; rows past wire_rows
+              // (a punctured code) and escapes take the rare branches
+              const uint32_t row0 = (uint32_t)(cc + C * S::natural(b * RL));
+              constexpr uint32_t rstep = (uint32_t)(C * (S::L / RL));
+              uint16_t* o = static_cast<uint16_t*>(a.out) + (size_t)row0 * ld + col;
+              const size_t step = (size_t)rstep * ld;
+              const bool all_rows = a.wire_rows >= C * S::L;
 #pragma unroll
-            for (int q = 0; q < RL; ++q) o[bitrev(q, BL) * step] = m_to_p(x[q]);
+              for (int q = 0; q < RL; ++q) {
+                const uint32_t v = m_to_p(x[q]);
+                const uint32_t row = row0 + bitrev(q, BL) * rstep;
+                if (all_rows || row < (uint32_t)a.wire_rows) {
+                  o[bitrev(q, BL) * step] = (uint16_t)v;
+                  if (v == 65536u) WireOut::make(a).escape(row, col);
+                }
+              }
+            } else {
+              uint32_t* o = out + (size_t)(cc + C * S::natural(b * RL)) * ld + col;
+              const size_t step = (size_t)C * (S::L / RL) * ld;
+#pragma unroll
+              for (int q = 0; q < RL; ++q) o[bitrev(q, BL) * step] = m_to_p(x[q]);
+            }
           }
         }
       }

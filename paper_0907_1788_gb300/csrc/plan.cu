@@ -601,8 +601,21 @@ int prepare_pattern(fnt_rs_plan_s* p, const uint32_t* positions, uint32_t npos, 
 // encode / decode / fnt dispatch
 // ---------------------------------------------------------------------------
 // TMA-staged encode (cluster-launch-control tile scheduling); returns 1 if it was not applicable.
+// Points an encode's output at the 16-bit wire matrix (columns from c0 on).
+static void set_wire(KArgs& a, const WireSpec* w, size_t c0) {
+  if (!w) return;
+  a.out = w->enc + c0;
+  a.ld_out = w->ld;
+  a.wire = 1;
+  a.wire_rows = (int)w->rows;
+  a.col_base = (int)(w->col0 + c0);
+  a.esc = w->esc;
+  a.esc_count = w->count;
+  a.esc_cap = w->cap;
+}
+
 static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                      size_t ld_enc, size_t W, cudaStream_t st) {
+                      size_t ld_enc, size_t W, cudaStream_t st, const WireSpec* wire) {
   if (p->no_tma || p->enc_L == 0 || p->u != 1) return 1;
   if ((reinterpret_cast<uintptr_t>(src) % 16) != 0 || (ld_src * 2) % 16 != 0) return 1;
   auto fn = tmap_encode_fn();
@@ -631,6 +644,7 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   a.C = C;
   a.twf = p->tenc.twf;
   a.status = p->status;
+  set_wire(a, wire, 0);
   TmaEncodeArgs t;
   t.twc = p->twc;
   t.rows_staged = rows_staged;
@@ -642,15 +656,16 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
 }
 
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                     size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
+                     size_t ld_enc, size_t W, void* workspace, cudaStream_t st,
+                     const WireSpec* wire) {
   const int sched = sched_effective(p, FNT_RS_OP_ENCODE);
   if (sched == FNT_RS_SCHED_TMA) {
-    const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st);
+    const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st, wire);
     if (t != 1) return t;  // else (unaligned pointers) the one-CTA tile below
   }
   if (sched == FNT_RS_SCHED_SPLIT)
     return do_encode_two_pass(p, src, ld_src, enc, ld_enc, W, static_cast<uint32_t*>(workspace),
-                              st);
+                              st, wire);
   KArgs a;
   a.in = src;
   a.ld_in = ld_src;
@@ -665,13 +680,15 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
   a.C = 1;
   a.twf = p->tn.twf;
   a.twi = p->tn.twi;
+  set_wire(a, wire, 0);
   tile_ops((int)p->n).encode(a, 1, st);
   return cuda_ok(cudaGetLastError());
 }
 
 int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                       size_t ld_enc, size_t W, uint32_t* workspace, cudaStream_t st) {
-  if (p->n <= 8192) return do_encode(p, src, ld_src, enc, ld_enc, W, nullptr, st);
+                       size_t ld_enc, size_t W, uint32_t* workspace, cudaStream_t st,
+                       const WireSpec* wire) {
+  if (p->n <= 8192) return do_encode(p, src, ld_src, enc, ld_enc, W, nullptr, st, wire);
   const size_t wc = split_chunk(p->n, 1);
   uint32_t* work = static_cast<uint32_t*>(workspace);
   for (size_t c0 = 0; c0 < W; c0 += wc) {
@@ -679,7 +696,7 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
     KArgs a;
     a.in = src + c0;
     a.ld_in = ld_src;
-    a.out = enc + c0;
+    a.out = enc ? enc + c0 : nullptr;  // (the wire output replaces it)
     a.ld_out = ld_enc;
     a.out2 = work;
     a.ld_work = (size_t)w;
@@ -698,6 +715,7 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
     b.ld_in = (size_t)w;
     b.twf = p->tl.twf;
     b.twi = p->tl.twi;
+    set_wire(b, wire, c0);
     local_launcher(false, LM_ENC)(b, p->C_local, st);
   }
   return cuda_ok(cudaGetLastError());
@@ -1026,6 +1044,7 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
   if (cudaMalloc(&p->pscratch, p->pscratch_words * 4) != cudaSuccess) return fail(FNT_RS_E_CUDA);
   for (auto& sl : p->slots)
     if ((rc = alloc_pattern_tables(sl, n, true))) return fail(rc);
+  if ((rc = pipe_init(p->pipe))) return fail(rc);
   if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return fail(FNT_RS_E_CUDA);
   *out = p;
   return FNT_RS_OK;
@@ -1040,6 +1059,7 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   cudaFree(p->ghat);
   for (auto& sl : p->slots) free_pattern_tables(sl);
   free_pattern_tables(p->sys);
+  pipe_free(p->pipe);
   delete p;
 }
 
@@ -1053,14 +1073,12 @@ size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
     case FNT_RS_OP_DECODE_SYS: return sys_workspace_bytes(p, W);
     case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf_max(p));
     case FNT_RS_OP_FNT: return ws_bytes(p, W, fnt_nbuf(p));
-    case FNT_RS_OP_ENCODE_HOST: {
-      const size_t stage = align256((size_t)p->k * W * 2) + align256((size_t)p->n_out * W * 4);
-      return stage + fnt_rs_workspace_bytes(p, W, FNT_RS_OP_ENCODE);
-    }
-    case FNT_RS_OP_DECODE_HOST: {
-      const size_t stage = ((size_t)p->k * W * 4 + 255) / 256 * 256 + ((size_t)p->k * W * 2 + 255) / 256 * 256;
-      return stage + ws_bytes(p, W, dec_nbuf_max(p));
-    }
+    case FNT_RS_OP_ENCODE_HOST:
+    case FNT_RS_OP_DECODE_HOST:
+    case FNT_RS_OP_ENCODE_WIRE_HOST:
+    case FNT_RS_OP_DECODE_WIRE_HOST: return host_workspace_bytes(p, W, op);
+    case FNT_RS_OP_ENCODE_WIRE:
+    case FNT_RS_OP_DECODE_WIRE: return wire_workspace_bytes(p, W, op);
     default: return 0;
   }
 }
@@ -1211,41 +1229,6 @@ int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, s
   if (!aligned(in, 4) || !aligned(out, 4)) return FNT_RS_E_ARG;
   if (ws_bytes(p, W, fnt_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
   return fnt_columns(p, in, ld_in, out, ld_out, W, inverse != 0, workspace, S(stream));
-}
-
-int fnt_rs_encode_host(fnt_rs_plan p, const uint16_t* h_src, uint32_t* h_enc, size_t W,
-                       void* workspace, void* stream) {
-  if (!p || !h_src || !h_enc || !workspace) return FNT_RS_E_ARG;
-  if (W == 0) return FNT_RS_OK;
-  cudaStream_t st = S(stream);
-  uint8_t* ws = static_cast<uint8_t*>(workspace);
-  uint16_t* d_src = reinterpret_cast<uint16_t*>(ws);
-  uint32_t* d_enc = reinterpret_cast<uint32_t*>(ws + align256((size_t)p->k * W * 2));
-  void* rest = reinterpret_cast<uint8_t*>(d_enc) + align256((size_t)p->n_out * W * 4);
-  int rc = cuda_ok(cudaMemcpyAsync(d_src, h_src, (size_t)p->k * W * 2, cudaMemcpyHostToDevice, st));
-  if (rc) return rc;
-  if ((rc = fnt_rs_encode(p, d_src, W, d_enc, W, W, rest, stream))) return rc;
-  if ((rc = cuda_ok(cudaMemcpyAsync(h_enc, d_enc, (size_t)p->n_out * W * 4,
-                                    cudaMemcpyDeviceToHost, st))))
-    return rc;
-  return cuda_ok(cudaStreamSynchronize(st));
-}
-
-int fnt_rs_decode_host(fnt_rs_plan p, const uint32_t* h_recv, const uint32_t* positions,
-                       uint32_t npos, uint16_t* h_out, size_t W, void* workspace, void* stream) {
-  if (!p || !h_recv || !h_out || !workspace) return FNT_RS_E_ARG;
-  if (W == 0) return FNT_RS_OK;
-  cudaStream_t st = S(stream);
-  uint8_t* ws = static_cast<uint8_t*>(workspace);
-  uint32_t* d_recv = reinterpret_cast<uint32_t*>(ws);
-  uint16_t* d_out = reinterpret_cast<uint16_t*>(ws + ((size_t)p->k * W * 4 + 255) / 256 * 256);
-  void* rest = reinterpret_cast<uint8_t*>(d_out) + ((size_t)p->k * W * 2 + 255) / 256 * 256;
-  int rc = cuda_ok(cudaMemcpyAsync(d_recv, h_recv, (size_t)p->k * W * 4, cudaMemcpyHostToDevice, st));
-  if (rc) return rc;
-  if ((rc = fnt_rs_decode(p, d_recv, W, positions, npos, d_out, W, W, rest, stream))) return rc;
-  if ((rc = cuda_ok(cudaMemcpyAsync(h_out, d_out, (size_t)p->k * W * 2, cudaMemcpyDeviceToHost, st))))
-    return rc;
-  return cuda_ok(cudaStreamSynchronize(st));
 }
 
 int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
