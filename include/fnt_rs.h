@@ -226,11 +226,14 @@ int fnt_rs_fnt(fnt_rs_plan plan, const uint32_t* in, size_t ld_in, uint32_t* out
 /*
  * Host-buffer variants: same results as fnt_rs_encode / fnt_rs_decode with
  * host source and destination buffers (pinned memory gives asynchronous
- * copies).  The host-to-device copy, the kernels and the device-to-host copy
- * are enqueued on `stream` and the call synchronises the stream before
- * returning.  workspace: device, fnt_rs_workspace_bytes(plan, W,
- * FNT_RS_OP_ENCODE_HOST / FNT_RS_OP_DECODE_HOST) bytes; it also stages the
- * data.  Host buffers are dense (ld = W).
+ * copies).  Batches of W >= 1024 codewords are cut into up to 4 column
+ * chunks whose host-to-device copies, kernels and device-to-host copies
+ * overlap: the kernels run on `stream`, the copies on two streams the plan
+ * owns, ordered after the work already queued on `stream`; the call
+ * synchronises `stream` before returning, with every copy done.  workspace:
+ * device, fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_ENCODE_HOST /
+ * FNT_RS_OP_DECODE_HOST) bytes; it also stages the data.  Host buffers are
+ * dense (ld = W).  A plan's host-buffer calls must not run concurrently.
  */
 int fnt_rs_encode_host(fnt_rs_plan plan, const uint16_t* h_src, uint32_t* h_enc, size_t W,
                        void* workspace, void* stream);
@@ -346,9 +349,8 @@ int fnt_rs_decode_wire(fnt_rs_plan plan, const uint16_t* recv, size_t ld_recv,
                        void* stream);
 
 /*
- * Host-buffer variants of the wire calls (dense host buffers, ld = W; the
- * copies, the kernels and the escape handling are enqueued on `stream`,
- * which the call synchronises).  Encode: h_enc [n_out][W] uint16; the
+ * Host-buffer variants of the wire calls (dense host buffers, ld = W;
+ * chunked and synchronised like fnt_rs_encode_host / fnt_rs_decode_host).  Encode: h_enc [n_out][W] uint16; the
  * escapes are written to h_esc sorted by row, then column, and their number
  * to *nesc.  Returns FNT_RS_E_ARG if they do not fit in esc_cap (*nesc then
  * says how many there are) and FNT_RS_E_WORKSPACE if they exceed
