@@ -76,19 +76,26 @@ def encode_instr(n: int, k: int) -> float:
     return 2 * fnt_instr(n // 2) + 3 * (n // 2) + 4 * n
 
 
+# Sources that make up the device code of the workload's kernels (k_encode_tma,
+# k_plan_fused, k_decode_tma at n = 8192): the kernel templates, the headers they
+# include and the translation unit that instantiates them.
+KERNEL_SOURCES = ("field.cuh", "tile.cuh", "kernels.cuh", "kargs.h", "logplan.cuh", "tma.cuh",
+                  "sched.h", "inst.cuh", "inst_big.cu")
+
+
 def _src_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0907_1788_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the sources still match."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
