@@ -403,6 +403,47 @@ def wire_measure(pkg, dev, reps=20):
                       "erasure pattern (cached); L2 flushed"}
 
 
+def paper_route_measure(pkg, dev, reps=10):
+    """The paper's own decode route (chirp / middle products at length 2n, 4 FNT_2n per
+    codeword) against the default decode (3 FNT_n) on the headline shape."""
+    import torch
+
+    cfg = WORKLOAD
+    n, k, W = cfg.n, cfg.k, cfg.W
+    pos = cfg.positions()
+    src = cfg.source()
+    out = torch.empty((k, W), dtype=torch.int16, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, sched in (("default", None), ("paper", pkg.SCHED_PAPER)):
+        plan = pkg.Plan(n, k, device=dev)
+        if sched is not None:
+            plan.set_schedule(pkg.OP_DECODE, sched)
+        enc = plan.encode(pkg.to_device(src, dev))
+        recv = torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
+        ws = plan.workspace(W, pkg.OP_DECODE)
+        plan.prepare(pos)
+        for _ in range(3):
+            pkg.fnt_rs_decode(plan.handle, recv, pos, out, ws)
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            pkg.fnt_rs_decode(plan.handle, recv, pos, out, ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ok = np.array_equal(pkg.to_host(out), src) and plan.status() == 0
+        res[name] = {"decode_ms": statistics.median(ts), "round_trip_ok": bool(ok),
+                     "workspace_mb": (0 if ws is None else ws.numel()) / 1e6}
+        plan.close()
+    res["paper_over_default"] = res["paper"]["decode_ms"] / res["default"]["decode_ms"]
+    res["transforms_per_codeword"] = {"default": "3 FNT_n", "paper": "4 FNT_2n (~8 FNT_n)"}
+    res["config"] = f"{cfg.name}, pattern cached, L2 flushed"
+    return res
+
+
 def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
     """The cfg5 arrival rates, each on the head of its seeded trace, plus a
     fresh-pattern variant (every decode request brings a new erasure pattern)."""
@@ -698,6 +739,7 @@ def run_gpu(args):
         line["serving"] = serving_sweep(pkg, count=args.serving_requests)
         line["systematic"] = systematic_measure(pkg, dev)
         line["wire"] = wire_measure(pkg, dev)
+        line["paper_route"] = paper_route_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

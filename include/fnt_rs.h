@@ -123,7 +123,16 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *                       passes through the workspace (encode n > 8192,
  *                       decode n >= 16384),
  *   FNT_RS_SCHED_CPA    decode only: half-width tiles staged by cp.async,
- *                       two CTAs per SM (n = 4096 or 8192, k <= n/2).
+ *                       two CTAs per SM (n = 4096 or 8192, k <= n/2),
+ *   FNT_RS_SCHED_PAPER  decode only: the paper's own route (Sec. II.B/III):
+ *                       step 3 by the chirp (per pattern), step 5 as a
+ *                       middle product and step 6 as a product, both by
+ *                       FNT_2n -- 4 FNT_2n per codeword against the 3 FNT_n
+ *                       of the other schedules; for comparison (n <= 32768,
+ *                       k <= n/2, default root).  Selecting it builds its
+ *                       tables (synchronising the device) and grows the
+ *                       decode workspace by 2 * 2n * W * 4 bytes (query the
+ *                       size after selecting it); the autotuner never picks it.
  * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else TILE
  * (encode up to n = 8192; decode wherever one CTA holds the codeword), else
  * SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
@@ -133,7 +142,8 @@ enum fnt_rs_sched {
   FNT_RS_SCHED_TMA = 1,
   FNT_RS_SCHED_TILE = 2,
   FNT_RS_SCHED_SPLIT = 3,
-  FNT_RS_SCHED_CPA = 4
+  FNT_RS_SCHED_CPA = 4,
+  FNT_RS_SCHED_PAPER = 5
 };
 
 typedef struct fnt_rs_tune_result_s {

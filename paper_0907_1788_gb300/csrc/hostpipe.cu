@@ -120,13 +120,13 @@ size_t host_workspace_bytes(fnt_rs_plan_s* p, size_t W, int op) {
       return align256(k * W * 2) + align256(n_out * W * 4) +
              fnt_rs_workspace_bytes(p, W, FNT_RS_OP_ENCODE);
     case FNT_RS_OP_DECODE_HOST:
-      return align256(k * W * 4) + align256(k * W * 2) + ws_bytes(p, W, dec_nbuf_max(p));
+      return align256(k * W * 4) + align256(k * W * 2) + dec_ws_max(p, W);
     case FNT_RS_OP_ENCODE_WIRE_HOST:
       return align256(k * W * 2) + align256(n_out * W * 2) +
              align256(fnt_rs_wire_escape_cap(p, W) * 8) + 256 + ws_bytes(p, W, enc_nbuf_max(p));
     case FNT_RS_OP_DECODE_WIRE_HOST:
       return align256(k * W * 2) + align256((size_t)kEscStage * 8) + align256(k * W * 2) +
-             align256(k * W * 4) + ws_bytes(p, W, dec_nbuf_max(p));
+             align256(k * W * 4) + dec_ws_max(p, W);
     default: return 0;
   }
 }

@@ -55,6 +55,7 @@ int pipe_init(HostPipe& h);
 void pipe_free(HostPipe& h);
 
 constexpr int kPatternSlots = 4;
+struct PaperState;  // paper_route.cu
 constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
 
 }  // namespace fntrs
@@ -91,6 +92,7 @@ struct fnt_rs_plan_s {
   fntrs::PatternSlot sys;     // pattern of positions 0..k-1 (systematic code), built on first use
   bool sys_ready = false;
   fntrs::HostPipe pipe;       // host-buffer entry points
+  fntrs::PaperState* paper = nullptr;  // decode schedule FNT_RS_SCHED_PAPER, once selected
 };
 
 namespace fntrs {
@@ -166,5 +168,18 @@ int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* en
 int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
                      cudaStream_t st, int slots, uint32_t* out32 = nullptr);
+// decode workspace: of the schedule in use / of every schedule the plan can run
+size_t dec_ws_now(const fnt_rs_plan_s* p, size_t W);
+size_t dec_ws_max(const fnt_rs_plan_s* p, size_t W);
+
+// The paper's decode route (paper_route.cu): chirp step 3 and middle-product
+// step 5 at length 2n, step 6 by FNT_2n.
+bool paper_available(const fnt_rs_plan_s* p);
+int paper_enable(fnt_rs_plan_s* p, cudaStream_t st);
+void paper_free(fnt_rs_plan_s* p);
+size_t paper_ws_bytes(const fnt_rs_plan_s* p, size_t W);
+int paper_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, size_t ld_recv,
+                 uint16_t* out, size_t ld_out, size_t W, void* workspace, cudaStream_t st,
+                 int slots, uint32_t* out32);
 
 }  // namespace fntrs

@@ -278,6 +278,7 @@ bool sched_available(const fnt_rs_plan_s* p, int op, int s) {
                                     !p->split;
       case FNT_RS_SCHED_TILE: return !p->split;
       case FNT_RS_SCHED_SPLIT: return n >= 16384;
+      case FNT_RS_SCHED_PAPER: return paper_available(p);
       default: return false;
     }
   }
@@ -304,6 +305,14 @@ int dec_nbuf(const fnt_rs_plan_s* p) {
 int enc_nbuf_max(const fnt_rs_plan_s* p) { return p->n > 8192 ? 1 : 0; }
 int dec_nbuf_max(const fnt_rs_plan_s* p) { return p->n >= 16384 ? (p->blocked ? 4 : 2) : 0; }
 int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
+
+size_t dec_ws_now(const fnt_rs_plan_s* p, size_t W) {
+  if (sched_effective(p, FNT_RS_OP_DECODE) == FNT_RS_SCHED_PAPER) return paper_ws_bytes(p, W);
+  return ws_bytes(p, W, dec_nbuf(p));
+}
+size_t dec_ws_max(const fnt_rs_plan_s* p, size_t W) {
+  return std::max(ws_bytes(p, W, dec_nbuf_max(p)), paper_ws_bytes(p, W));
+}
 
 static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
@@ -802,6 +811,8 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
                      size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, void* workspace,
                      cudaStream_t st, int slots, uint32_t* out32) {
   const int sched = sched_effective(p, FNT_RS_OP_DECODE);
+  if (sched == FNT_RS_SCHED_PAPER)
+    return paper_decode(p, sl, recv, ld_recv, out, ld_out, W, workspace, st, slots, out32);
   if (!slots && sched == FNT_RS_SCHED_TMA) {
     const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st, out32);
     if (t != 1) return t;  // else (unaligned rows) the one-CTA tile below
@@ -1060,6 +1071,7 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   for (auto& sl : p->slots) free_pattern_tables(sl);
   free_pattern_tables(p->sys);
   pipe_free(p->pipe);
+  paper_free(p);
   delete p;
 }
 
@@ -1071,7 +1083,7 @@ size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
              (p->n_out < p->n ? align256((size_t)p->n * W * 4) : 0);
     case FNT_RS_OP_ENCODE_SYS:
     case FNT_RS_OP_DECODE_SYS: return sys_workspace_bytes(p, W);
-    case FNT_RS_OP_DECODE: return ws_bytes(p, W, dec_nbuf_max(p));
+    case FNT_RS_OP_DECODE: return dec_ws_max(p, W);
     case FNT_RS_OP_FNT: return ws_bytes(p, W, fnt_nbuf(p));
     case FNT_RS_OP_ENCODE_HOST:
     case FNT_RS_OP_DECODE_HOST:
@@ -1115,7 +1127,7 @@ int fnt_rs_decode(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv, const uin
   if (!p) return FNT_RS_E_ARG;
   if (!recv || !out || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(recv, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
-  if (ws_bytes(p, W, dec_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  if (dec_ws_now(p, W) && !workspace) return FNT_RS_E_WORKSPACE;
   int rc = prepare(p, positions, npos, S(stream));
   if (rc) return rc;
   if (W == 0) return FNT_RS_OK;
@@ -1129,7 +1141,7 @@ int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
   if (!p) return FNT_RS_E_ARG;
   if (!slots || !out || ld_slots < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(slots, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
-  if (ws_bytes(p, W, dec_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
+  if (dec_ws_now(p, W) && !workspace) return FNT_RS_E_WORKSPACE;
   if (p->u != 1) return FNT_RS_E_ROOT;  // slot rows follow the default root's positions
   int rc = prepare(p, positions, npos, S(stream));
   if (rc) return rc;
@@ -1234,6 +1246,10 @@ int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, s
 int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
   if (!p || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
   if (sched != FNT_RS_SCHED_AUTO && !sched_available(p, op, sched)) return FNT_RS_E_ARG;
+  if (sched == FNT_RS_SCHED_PAPER) {
+    const int rc = paper_enable(p, nullptr);
+    if (rc) return rc;
+  }
   (op == FNT_RS_OP_ENCODE ? p->sched_enc : p->sched_dec) = sched;
   return FNT_RS_OK;
 }

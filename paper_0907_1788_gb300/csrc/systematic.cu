@@ -95,7 +95,7 @@ bool aligned_to(const void* ptr, size_t a) { return reinterpret_cast<uintptr_t>(
 size_t sys_workspace_bytes(const fnt_rs_plan_s* p, size_t W) {
   if (W == 0) return 0;
   return 2 * align256((size_t)p->n * W * 4) +
-         std::max(ws_bytes(p, W, dec_nbuf_max(p)), fnt_columns_work_bytes(p, W));
+         std::max(dec_ws_max(p, W), fnt_columns_work_bytes(p, W));
 }
 
 }  // namespace fntrs

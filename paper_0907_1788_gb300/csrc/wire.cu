@@ -109,7 +109,7 @@ int wire_escapes(fnt_rs_plan_s* p, const uint2* esc, uint32_t nesc, uint32_t nre
 size_t wire_workspace_bytes(const fnt_rs_plan_s* p, size_t W, int op) {
   switch (op) {
     case FNT_RS_OP_ENCODE_WIRE: return ws_bytes(p, W, enc_nbuf_max(p));
-    case FNT_RS_OP_DECODE_WIRE: return dec_copy_bytes(p, W) + ws_bytes(p, W, dec_nbuf_max(p));
+    case FNT_RS_OP_DECODE_WIRE: return dec_copy_bytes(p, W) + dec_ws_max(p, W);
     default: return 0;
   }
 }
