@@ -346,6 +346,53 @@ def systematic_measure(pkg, dev, reps=20):
                       "(pattern cached) and with positions 0..k-1 received; L2 flushed"}
 
 
+def direct_measure(pkg, dev, n=512, k=256, W=2048, reps=20):
+    """The systematic code on a short code (k = 256, n = 512, 4 KB packets): the FNT
+    route against the paper's direct (quadratic) encoder and decoder."""
+    import torch
+
+    src = synth.source(11, k, W)
+    pos = synth.received_positions(n, synth.erased_uniform(12, n, k))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, sched in (("fnt", pkg.SCHED_AUTO), ("direct", pkg.SCHED_DIRECT)):
+        plan = pkg.Plan(n, k, device=dev)
+        plan.set_schedule(pkg.OP_ENCODE_SYS, sched)
+        plan.set_schedule(pkg.OP_DECODE_SYS, sched)
+        d_src = pkg.to_device(src, dev)
+        enc = torch.empty((n, W), dtype=torch.int32, device=dev)
+        out = torch.empty((k, W), dtype=torch.int16, device=dev)
+        ws_e = plan.workspace(W, pkg.OP_ENCODE_SYS)
+        ws_d = plan.workspace(W, pkg.OP_DECODE_SYS)
+        pkg.fnt_rs_encode_sys(plan.handle, d_src, enc, ws_e)
+        recv = torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            ts = []
+            for i in range(reps):
+                flush.fill_(i & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+
+        te = timed(lambda: pkg.fnt_rs_encode_sys(plan.handle, d_src, enc, ws_e))
+        td = timed(lambda: pkg.fnt_rs_decode_sys(plan.handle, recv, pos, out, ws_d))
+        ok = np.array_equal(pkg.to_host(out), src) and plan.status() == 0
+        gb = k * W * 2 / 1e9
+        res[name] = {"encode_sys_ms": te, "decode_sys_ms": td, "encode_gbs": gb / (te * 1e-3),
+                     "decode_gbs": gb / (td * 1e-3), "round_trip_ok": bool(ok)}
+        plan.close()
+    res["config"] = (f"k={k}, n={n}, W={W} (4 KB packets), systematic code, uniform erasures "
+                     "(pattern cached), L2 flushed")
+    return res
+
+
 def wire_measure(pkg, dev, reps=20):
     """16-bit wire format on the headline shape: device encode to 16-bit symbols +
     escapes, and decode from them (pattern cached), against the 32-bit calls."""
@@ -740,6 +787,7 @@ def run_gpu(args):
         line["systematic"] = systematic_measure(pkg, dev)
         line["wire"] = wire_measure(pkg, dev)
         line["paper_route"] = paper_route_measure(pkg, dev)
+        line["direct"] = direct_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -143,7 +143,8 @@ enum fnt_rs_sched {
   FNT_RS_SCHED_TILE = 2,
   FNT_RS_SCHED_SPLIT = 3,
   FNT_RS_SCHED_CPA = 4,
-  FNT_RS_SCHED_PAPER = 5
+  FNT_RS_SCHED_PAPER = 5,
+  FNT_RS_SCHED_DIRECT = 6
 };
 
 typedef struct fnt_rs_tune_result_s {
@@ -153,7 +154,16 @@ typedef struct fnt_rs_tune_result_s {
 
 /* Forces the schedule of `op` (FNT_RS_OP_ENCODE or FNT_RS_OP_DECODE);
  * FNT_RS_E_ARG if it cannot run this plan.  FNT_RS_SCHED_AUTO restores the
- * default choice. */
+ * default choice.  For FNT_RS_OP_ENCODE_SYS / FNT_RS_OP_DECODE_SYS the
+ * choices are FNT_RS_SCHED_AUTO (the FNT route) and FNT_RS_SCHED_DIRECT, the
+ * paper's quadratic methods for short codes (Sec. III, Tables I-II): the
+ * encoder computes the n_out - k non-systematic symbols as products by the
+ * (n - k) x k matrix of the Lagrange basis of r^0..r^(k-1) evaluated at r^j
+ * (built on the host when selected); the decoder copies the received source
+ * symbols and computes each missing one as a product by the Lagrange basis of
+ * the first k received positions at r^m (built on the host once per erasure
+ * pattern, then uploaded on `stream`).  Neither needs a workspace; k <= 1024,
+ * n <= 16384, default root; same results as the FNT route. */
 int fnt_rs_set_schedule(fnt_rs_plan plan, int op, int sched);
 /* The schedule `op` runs with now (never FNT_RS_SCHED_AUTO), or a negative error. */
 int fnt_rs_get_schedule(fnt_rs_plan plan, int op);

@@ -26,8 +26,9 @@ OP_ENCODE, OP_DECODE, OP_FNT, OP_ENCODE_HOST, OP_DECODE_HOST = 0, 1, 2, 3, 4
 OP_ENCODE_SYS, OP_DECODE_SYS = 5, 6
 OP_ENCODE_WIRE, OP_DECODE_WIRE, OP_ENCODE_WIRE_HOST, OP_DECODE_WIRE_HOST = 7, 8, 9, 10
 SCHED_AUTO, SCHED_TMA, SCHED_TILE, SCHED_SPLIT, SCHED_CPA, SCHED_PAPER = 0, 1, 2, 3, 4, 5
+SCHED_DIRECT = 6
 SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split", SCHED_CPA: "cpa",
-               SCHED_PAPER: "paper"}
+               SCHED_PAPER: "paper", SCHED_DIRECT: "direct"}
 
 E_RANGE = -7
 E_TIMEOUT = -8

@@ -23,7 +23,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 SOURCES = ["plan.cu", "pattern.cu", "inst_small.cu", "inst_mid.cu", "inst_big.cu",
            "inst_huge.cu", "inst_split.cu", "noalloc.cu", "ragged.cu", "ragged_kernel.cu", "server.cu",
            "systematic.cu", "wire.cu",
-           "hostpipe.cu", "paper_route.cu"]
+           "hostpipe.cu", "paper_route.cu",
+           "direct.cu"]
 
 
 def nvcc() -> str:

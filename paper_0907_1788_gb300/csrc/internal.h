@@ -55,7 +55,8 @@ int pipe_init(HostPipe& h);
 void pipe_free(HostPipe& h);
 
 constexpr int kPatternSlots = 4;
-struct PaperState;  // paper_route.cu
+struct PaperState;   // paper_route.cu
+struct DirectState;  // direct.cu
 constexpr size_t kChunkBudget = 96ull << 20;  // bytes of split-transform workspace per chunk
 
 }  // namespace fntrs
@@ -93,6 +94,8 @@ struct fnt_rs_plan_s {
   bool sys_ready = false;
   fntrs::HostPipe pipe;       // host-buffer entry points
   fntrs::PaperState* paper = nullptr;  // decode schedule FNT_RS_SCHED_PAPER, once selected
+  fntrs::DirectState* direct = nullptr;  // FNT_RS_SCHED_DIRECT of the systematic ops
+  int sched_sys_enc = 0, sched_sys_dec = 0;  // 0 (FNT route) or FNT_RS_SCHED_DIRECT
 };
 
 namespace fntrs {
@@ -181,5 +184,15 @@ size_t paper_ws_bytes(const fnt_rs_plan_s* p, size_t W);
 int paper_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, size_t ld_recv,
                  uint16_t* out, size_t ld_out, size_t W, void* workspace, cudaStream_t st,
                  int slots, uint32_t* out32);
+
+// The direct (quadratic) systematic encoder and decoder (direct.cu).
+bool direct_available(const fnt_rs_plan_s* p);
+int direct_enable(fnt_rs_plan_s* p);
+void direct_free(fnt_rs_plan_s* p);
+int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                      size_t ld_enc, size_t W, cudaStream_t st);
+int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
+                      const uint32_t* positions, uint16_t* out, size_t ld_out, size_t W,
+                      cudaStream_t st);
 
 }  // namespace fntrs

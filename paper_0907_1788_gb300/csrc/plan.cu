@@ -1072,6 +1072,7 @@ void fnt_rs_plan_destroy(fnt_rs_plan p) {
   free_pattern_tables(p->sys);
   pipe_free(p->pipe);
   paper_free(p);
+  direct_free(p);
   delete p;
 }
 
@@ -1244,6 +1245,16 @@ int fnt_rs_fnt(fnt_rs_plan p, const uint32_t* in, size_t ld_in, uint32_t* out, s
 }
 
 int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
+  if (p && (op == FNT_RS_OP_ENCODE_SYS || op == FNT_RS_OP_DECODE_SYS)) {
+    if (sched != FNT_RS_SCHED_AUTO && sched != FNT_RS_SCHED_DIRECT) return FNT_RS_E_ARG;
+    if (sched == FNT_RS_SCHED_DIRECT) {
+      if (!direct_available(p)) return FNT_RS_E_ARG;
+      const int rc = direct_enable(p);
+      if (rc) return rc;
+    }
+    (op == FNT_RS_OP_ENCODE_SYS ? p->sched_sys_enc : p->sched_sys_dec) = sched;
+    return FNT_RS_OK;
+  }
   if (!p || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
   if (sched != FNT_RS_SCHED_AUTO && !sched_available(p, op, sched)) return FNT_RS_E_ARG;
   if (sched == FNT_RS_SCHED_PAPER) {
@@ -1255,6 +1266,11 @@ int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
 }
 
 int fnt_rs_get_schedule(fnt_rs_plan p, int op) {
+  if (p && (op == FNT_RS_OP_ENCODE_SYS || op == FNT_RS_OP_DECODE_SYS)) {
+    const int s = op == FNT_RS_OP_ENCODE_SYS ? p->sched_sys_enc : p->sched_sys_dec;
+    // the FNT route interpolates with the decode schedule
+    return s ? s : sched_effective(p, FNT_RS_OP_DECODE);
+  }
   if (!p || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
   return sched_effective(p, op);
 }

@@ -116,8 +116,10 @@ int fnt_rs_encode_sys(fnt_rs_plan p, const uint16_t* src, size_t ld_src, uint32_
   if (!src || !enc || ld_src < W || ld_enc < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned_to(src, 2) || !aligned_to(enc, 4)) return FNT_RS_E_ARG;
   if (p->u != 1) return FNT_RS_E_ROOT;  // positions 0..k-1 are those of the default root
-  if (!workspace) return FNT_RS_E_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p->sched_sys_enc == FNT_RS_SCHED_DIRECT)
+    return direct_encode_sys(p, src, ld_src, enc, ld_enc, W, st);
+  if (!workspace) return FNT_RS_E_WORKSPACE;
   const size_t n = p->n, k = p->k;
   const SysWs w = sys_split(p, W, workspace);
   int rc = sys_pattern(p, st);
@@ -155,6 +157,8 @@ int fnt_rs_decode_sys(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv,
     count_launch();
     return cuda_ok(cudaGetLastError());
   }
+  if (p->sched_sys_dec == FNT_RS_SCHED_DIRECT)
+    return direct_decode_sys(p, recv, ld_recv, positions, out, ld_out, W, st);
   if (!workspace) return FNT_RS_E_WORKSPACE;
   const SysWs w = sys_split(p, W, workspace);
   if (n > k && (rc = cuda_ok(cudaMemsetAsync(w.Z + k * W, 0, (n - k) * W * 4, st)))) return rc;

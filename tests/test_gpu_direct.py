@@ -1,0 +1,103 @@
+"""The direct (quadratic) systematic encoder and decoder (Sec. III, Tables I-II)
+on the GPU vs the CPU oracle, bit-exact: the same systematic code as the FNT
+route (oracle.encode_sys / oracle.decode_sys), computed as products by
+Lagrange-basis matrices."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+P = 65537
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_0907_1788_gb300 import build
+
+    build.build()
+    import paper_0907_1788_gb300 as pkg
+
+    pkg.load()
+    oracle.build()
+    return pkg
+
+
+def _direct_plan(pkg, n, k):
+    plan = pkg.Plan(n, k)
+    plan.set_schedule(pkg.OP_ENCODE_SYS, pkg.SCHED_DIRECT)
+    plan.set_schedule(pkg.OP_DECODE_SYS, pkg.SCHED_DIRECT)
+    assert plan.schedule(pkg.OP_ENCODE_SYS) == pkg.SCHED_DIRECT
+    return plan
+
+
+@pytest.mark.parametrize("n,k,W", [(2, 1, 3), (16, 5, 9), (64, 20, 70), (512, 256, 130),
+                                   (1024, 1000, 16), (4096, 1024, 8)])
+def test_direct_encode_matches_oracle(pkg, n, k, W):
+    src = synth.source(n + k, k, W)
+    plan = _direct_plan(pkg, n, k)
+    enc = pkg.to_host(plan.encode_sys(pkg.to_device(src)))
+    assert np.array_equal(enc, oracle.encode_sys(src, n))
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("n,k,W", [(16, 5, 9), (64, 20, 70), (512, 256, 130), (4096, 1024, 8)])
+def test_direct_decode_matches_oracle(pkg, n, k, W):
+    seed = 3 * n + k
+    plan = _direct_plan(pkg, n, k)
+    src = synth.source(seed, k, W)
+    enc = pkg.to_host(plan.encode_sys(pkg.to_device(src)))
+    for kind in ("uniform", "burst"):
+        er = (synth.erased_uniform if kind == "uniform" else synth.erased_burst)(seed + 1, n, k)
+        pos = synth.received_positions(n, er)
+        out = pkg.to_host(plan.decode_sys(pkg.to_device(np.ascontiguousarray(enc[pos])), pos))
+        assert np.array_equal(out, src), kind
+    assert plan.status() == 0
+    # arbitrary received words: the interpolant's values at r^0..r^(k-1)
+    rng = np.random.default_rng(seed)
+    pos = rng.permutation(n)[:k].astype(np.uint32)
+    v = rng.integers(0, P, (k, W), dtype=np.uint32)
+    got = pkg.to_host(plan.decode_sys(pkg.to_device(v), pos))
+    want, flag = oracle.decode_sys(v, pos, n, k)
+    assert np.array_equal(got, want)
+    assert (plan.status() == pkg.E_RANGE) == flag
+
+
+def test_direct_equals_fnt_route_punctured_and_patterns(pkg):
+    n, k, W, n_out = 1024, 300, 40, 700
+    src = synth.source(5, k, W)
+    fnt = pkg.Plan(n, k)
+    fnt.set_length(n_out)
+    plan = _direct_plan(pkg, n, k)
+    plan.set_length(n_out)
+    e1 = pkg.to_host(plan.encode_sys(pkg.to_device(src)))
+    e2 = pkg.to_host(fnt.encode_sys(pkg.to_device(src)))
+    assert e1.shape[0] == n_out and np.array_equal(e1, e2)
+    rng = np.random.default_rng(6)
+    for _ in range(3):  # new patterns rebuild the decode matrix
+        pos = rng.permutation(n_out)[:k].astype(np.uint32)
+        d1 = pkg.to_host(plan.decode_sys(pkg.to_device(np.ascontiguousarray(e1[pos])), pos))
+        assert np.array_equal(d1, src)
+    # all source positions lost
+    pos = np.arange(k, n_out, dtype=np.uint32)[:k]
+    assert np.array_equal(pkg.to_host(plan.decode_sys(
+        pkg.to_device(np.ascontiguousarray(e1[pos])), pos)), src)
+    assert plan.status() == 0
+
+
+def test_direct_availability_and_switch_back(pkg):
+    plan = pkg.Plan(4096, 2048)  # k above the direct limit
+    with pytest.raises(pkg.FntRsError):
+        plan.set_schedule(pkg.OP_ENCODE_SYS, pkg.SCHED_DIRECT)
+    with pytest.raises(pkg.FntRsError):
+        pkg.Plan(256, 100).set_schedule(pkg.OP_ENCODE, pkg.SCHED_DIRECT)
+    plan = _direct_plan(pkg, 256, 100)
+    plan.set_schedule(pkg.OP_ENCODE_SYS, pkg.SCHED_AUTO)
+    assert plan.schedule(pkg.OP_ENCODE_SYS) != pkg.SCHED_DIRECT
+    src = synth.source(9, 100, 12)
+    assert np.array_equal(pkg.to_host(plan.encode_sys(pkg.to_device(src))),
+                          oracle.encode_sys(src, 256))
