@@ -355,7 +355,10 @@ def direct_measure(pkg, dev, n=512, k=256, W=2048, reps=20):
     pos = synth.received_positions(n, synth.erased_uniform(12, n, k))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     res = {}
-    for name, sched in (("fnt", pkg.SCHED_AUTO), ("direct", pkg.SCHED_DIRECT)):
+    for name, sched in (("fnt", pkg.SCHED_AUTO), ("direct", pkg.SCHED_DIRECT),
+                        ("direct_simt", pkg.SCHED_DIRECT)):
+        # the direct methods multiply on the tensor cores unless FNTRS_DIRECT_SIMT=1
+        os.environ["FNTRS_DIRECT_SIMT"] = "1" if name == "direct_simt" else "0"
         plan = pkg.Plan(n, k, device=dev)
         plan.set_schedule(pkg.OP_ENCODE_SYS, sched)
         plan.set_schedule(pkg.OP_DECODE_SYS, sched)
@@ -388,6 +391,9 @@ def direct_measure(pkg, dev, n=512, k=256, W=2048, reps=20):
         res[name] = {"encode_sys_ms": te, "decode_sys_ms": td, "encode_gbs": gb / (te * 1e-3),
                      "decode_gbs": gb / (td * 1e-3), "round_trip_ok": bool(ok)}
         plan.close()
+    os.environ.pop("FNTRS_DIRECT_SIMT", None)
+    res["products"] = {"direct": "tcgen05 BF16 limbs, FP32 accumulation in tensor memory",
+                       "direct_simt": "integer kernel (64-bit accumulation)"}
     res["config"] = (f"k={k}, n={n}, W={W} (4 KB packets), systematic code, uniform erasures "
                      "(pattern cached), L2 flushed")
     return res

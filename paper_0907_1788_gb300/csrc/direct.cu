@@ -13,9 +13,22 @@
 // L_i(x) = w_i A(x) / (x - x_i), A = prod (x - x_l), w_i = 1 / A'(x_i): the
 // matrices are built on the host in O(rows * k) (one batched inversion per
 // row) -- G once per plan, D once per erasure pattern -- and the products run in
-// a tiled integer kernel: 64-bit accumulation of the exact 17 x 32-bit products
-// (IMAD.WIDE), one reduction per output (2^32 = 1 mod p).
+// the 5th-generation tensor cores (tcgen05, below), with a tiled integer kernel
+// (64-bit accumulation of exact products on IMAD.WIDE) kept for comparison
+// (environment FNTRS_DIRECT_SIMT=1).
+//
+// Tensor-core product, exact over F_p: every operand is split into two signed
+// 8-bit limbs, x = lo + 256 hi with lo in [-128, 127] and hi in [-128, 128]
+// (matrix entries balanced to (-p/2, p/2], data centred by -32768), which BF16
+// holds exactly.  The four limb products accumulate in FP32 in tensor memory;
+// each term is at most 128 * 128 = 2^14 and K <= 1024 of them sum to at most
+// 2^24 in magnitude, so every partial sum is an exact FP32 integer.  The
+// epilogue forms c00 + 256 (c01 + c10) + 65536 c11 (65536 = -1 mod p), adds
+// 32768 times the row sum of the matrix for the centring and reduces mod p.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 
 #include <algorithm>
 #include <vector>
@@ -24,6 +37,7 @@
 #include "field.cuh"
 #include "internal.h"
 #include "kargs.h"
+#include "umma.cuh"
 
 namespace fntrs {
 
@@ -160,6 +174,180 @@ __global__ void __launch_bounds__(256) k_fp_gemm(const uint32_t* __restrict__ A,
   if (bad) atomicOr(status, ST_RANGE);
 }
 
+// ---- tensor-core product ---------------------------------------------------
+// Operand tiles of 128 rows x 64 K-values, K-major core-matrix layout (8 rows
+// x 8 values = 128 bytes per core matrix, 128 bytes apart along K, 1024 bytes
+// apart along the rows), the two limbs of a tile 16 KB apart: the global image
+// of one (row tile, K chunk) pair is exactly the 32 KB its shared-memory stage
+// holds.
+constexpr int kTcRows = 128, kTcK = 64, kTcTile = kTcRows * kTcK;  // elements per limb tile
+constexpr int kTcChunkBytes = 2 * kTcTile * 2;                     // both limbs, bf16
+constexpr int kTcSmem = 120 * 1024;  // more than half an SM: one CTA (and one TMEM user) per SM
+constexpr uint32_t kTcIdesc = idesc_bf16_f32<128, 128>();
+
+__device__ __forceinline__ int tc_off(int r, int k) {
+  return (r >> 3) * 512 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(int v) {  // |v| <= 256: exact
+  return __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+}
+
+// v in [-32768, 32768] -> v = lo + 256 hi, lo in [-128, 127], hi in [-128, 128]
+__device__ __forceinline__ void split_limbs(int v, int& lo, int& hi) {
+  lo = ((v + 128) & 255) - 128;
+  hi = (v - lo) / 256;
+}
+
+// limb tiles of A [M][K] (entries in [0, p), balanced); tile (mt, kc) at
+// ((mt * Kc + kc) * 2 + limb) * kTcTile
+__global__ void k_tc_limbs_a(const uint32_t* __restrict__ A, int M, int K, int Kc,
+                             uint16_t* __restrict__ out, size_t total) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = t / kTcTile;
+    const int e = (int)(t % kTcTile), r = e / kTcK, kk = e % kTcK;
+    const int mt = (int)(tile / Kc), kc = (int)(tile % Kc);
+    const int row = mt * kTcRows + r, col = kc * kTcK + kk;
+    int v = 0;
+    if (row < M && col < K) {
+      const uint32_t a = A[(size_t)row * K + col];
+      v = a > 32768u ? (int)a - 65537 : (int)a;
+    }
+    int lo, hi;
+    split_limbs(v, lo, hi);
+    uint16_t* o = out + tile * 2 * kTcTile + tc_off(r, kk);
+    o[0] = bf16_bits(lo);
+    o[kTcTile] = bf16_bits(hi);
+  }
+}
+
+// limb tiles of the data B [K][ld_b] seen as the N x K operand (row n = column
+// n of B), centred: x - 32768 with x = value mod p (received values above
+// 65536 raise the range flag)
+template <class TB>
+__global__ void k_tc_limbs_b(const TB* __restrict__ B, size_t ld_b, int K, int W, int Kc,
+                             uint16_t* __restrict__ out, size_t total, int* status) {
+  bool bad = false;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = t / kTcTile;
+    const int e = (int)(t % kTcTile), kk = e / kTcRows, r = e % kTcRows;  // r fastest: coalesced
+    const int nt = (int)(tile / Kc), kc = (int)(tile % Kc);
+    const int n = nt * kTcRows + r, k = kc * kTcK + kk;
+    int v = 0;
+    if (n < W && k < K) {
+      const uint32_t x = (uint32_t)B[(size_t)k * ld_b + n];
+      bad |= x > 65536u;
+      v = (int)m_to_p(x) - 32768;
+    }
+    int lo, hi;
+    split_limbs(v, lo, hi);
+    uint16_t* o = out + tile * 2 * kTcTile + tc_off(r, kk);
+    o[0] = bf16_bits(lo);
+    o[kTcTile] = bf16_bits(hi);
+  }
+  if (bad) atomicOr(status, ST_RANGE);
+}
+
+// C = A B over F_p for one 128 x 128 output tile: K in chunks of 64, each
+// chunk's limb tiles staged in shared memory and multiplied by one thread
+// issuing 4 K-steps x 4 limb pairs of 128x128x16 BF16 MMAs into four FP32
+// accumulators (all 512 tensor-memory columns).  Output as in k_fp_gemm.
+__global__ void __launch_bounds__(128, 1)
+    k_fp_gemm_tc(const uint16_t* __restrict__ Al, const uint16_t* __restrict__ Bl, int M, int Kc,
+                 int W, const uint32_t* __restrict__ corr, uint32_t* __restrict__ out32,
+                 size_t row0, uint16_t* __restrict__ out16, const uint32_t* __restrict__ mrow,
+                 size_t ld_out, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint16_t* sA = reinterpret_cast<uint16_t*>(base);
+  uint16_t* sB = reinterpret_cast<uint16_t*>(base + kTcChunkBytes);
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mt = blockIdx.y, nt = blockIdx.x;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (warp == 0) tmem_alloc(&tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = tslot;
+  const uint4* gA = reinterpret_cast<const uint4*>(Al + (size_t)mt * Kc * 2 * kTcTile);
+  const uint4* gB = reinterpret_cast<const uint4*>(Bl + (size_t)nt * Kc * 2 * kTcTile);
+  constexpr int kVec = kTcChunkBytes / 16;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int c = 0; c < Kc && ok; ++c) {
+    const uint4* a = gA + (size_t)c * kVec;
+    const uint4* b = gB + (size_t)c * kVec;
+    for (int i = threadIdx.x; i < kVec; i += 128) {
+      reinterpret_cast<uint4*>(sA)[i] = __ldg(a + i);
+      reinterpret_cast<uint4*>(sB)[i] = __ldg(b + i);
+    }
+    fence_proxy_async();  // the tensor cores read shared memory through the async proxy
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < kTcK / 16; ++s)
+#pragma unroll
+        for (int la = 0; la < 2; ++la)
+#pragma unroll
+          for (int lb = 0; lb < 2; ++lb) {
+            const uint64_t ad = smem_desc(sA + la * kTcTile + s * 128, 128, 1024);
+            const uint64_t bd = smem_desc(sB + lb * kTcTile + s * 128, 128, 1024);
+            mma_bf16(taddr + (uint32_t)(2 * la + lb) * 128u, ad, bd, kTcIdesc,
+                     (c > 0 || s > 0) ? 1u : 0u);
+          }
+      mma_commit(&bar);
+    }
+    // the stage is refilled (and the accumulators read) only after the MMAs finish
+    ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
+    ok = !__syncthreads_or(!ok);
+  }
+  if (ok) {
+    tc_fence_after();
+    const int r = mt * kTcRows + warp * 32 + lane;
+    const uint32_t lane_addr = taddr + ((uint32_t)(warp * 32) << 16);
+    const int64_t cr = r < M ? (int64_t)corr[r] : 0;
+    bool bad = false;
+    for (int j0 = 0; j0 < kTcRows; j0 += 16) {
+      float c00[16], c01[16], c10[16], c11[16];
+      tmem_ld16(lane_addr + 0u * 128u + (uint32_t)j0, c00);
+      tmem_ld16(lane_addr + 1u * 128u + (uint32_t)j0, c01);
+      tmem_ld16(lane_addr + 2u * 128u + (uint32_t)j0, c10);
+      tmem_ld16(lane_addr + 3u * 128u + (uint32_t)j0, c11);
+      if (r >= M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = nt * kTcRows + j0 + i;
+        if (col >= W) continue;
+        int64_t v = (int64_t)__float2int_rn(c00[i]) +
+                    256 * ((int64_t)__float2int_rn(c01[i]) + (int64_t)__float2int_rn(c10[i])) -
+                    (int64_t)__float2int_rn(c11[i]) + cr;
+        v %= 65537;
+        if (v < 0) v += 65537;
+        if (out32) {
+          out32[(row0 + r) * ld_out + col] = (uint32_t)v;
+        } else {
+          bad |= v > 65535;
+          out16[(size_t)mrow[r] * ld_out + col] = (uint16_t)(v > 65535 ? 0 : v);
+        }
+      }
+    }
+    if (bad) atomicOr(status, ST_RANGE);
+  } else if (threadIdx.x == 0) {
+    atomicOr(status, ST_TIMEOUT);
+    mbar_wait(&bar, phase ^ 1u);  // bounded: let MMAs still in flight finish
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, 512);
+}
+
 // encode: enc[i][c] = src[i][c], i < k
 __global__ void k_copy_src(const uint16_t* __restrict__ src, size_t ld_src, uint32_t* enc,
                            size_t ld_enc, int k, int W) {
@@ -210,7 +398,7 @@ int launch_gemm(const uint32_t* A, int M, int K, const TB* B, size_t ld_b, int W
 
 }  // namespace
 
-constexpr uint32_t kDirectMaxK = 1024;
+constexpr uint32_t kDirectMaxK = 1024;  // also the exactness bound of the tensor-core product
 constexpr uint32_t kDirectMaxN = 16384;
 
 struct DirectState {
@@ -218,13 +406,76 @@ struct DirectState {
   uint32_t* D = nullptr;     // [k][k] max: rows of the missing source symbols
   uint32_t* mrow = nullptr;  // [k]: output row of each D row
   uint2* cmap = nullptr;     // [k]: {received row, output row} of received source rows
+  uint32_t* gcorr = nullptr; // [n - k]: 32768 * row sum of G (the data centring), mod p
+  uint32_t* dcorr = nullptr; // [k]: the same for D
+  uint16_t* Gl = nullptr;    // limb tiles of G (tensor-core product)
+  uint16_t* Dl = nullptr;    // limb tiles of D
   std::vector<uint32_t> key;
   int nmiss = 0, ncopy = 0;
   bool pattern_ready = false;
+  bool simt = false;         // FNTRS_DIRECT_SIMT=1: the integer kernel instead
 };
+
+namespace {
+
+int tiles(int rows) { return (rows + kTcRows - 1) / kTcRows; }
+int kchunks(int K) { return (K + kTcK - 1) / kTcK; }
+size_t limb_bytes(int rows, int K) { return (size_t)tiles(rows) * kchunks(K) * kTcChunkBytes; }
+
+std::vector<uint32_t> centring(const std::vector<uint32_t>& rows, size_t k) {
+  const size_t m = k ? rows.size() / k : 0;
+  std::vector<uint32_t> c(m);
+  for (size_t t = 0; t < m; ++t) {
+    uint64_t acc = 0;
+    for (size_t l = 0; l < k; ++l) acc += rows[t * k + l];
+    c[t] = hm((uint32_t)(acc % kPh), 32768u);
+  }
+  return c;
+}
+
+int limbs_a(const fnt_rs_plan_s* p, const uint32_t* A, int M, int K, uint16_t* out,
+            cudaStream_t st) {
+  const size_t total = (size_t)tiles(M) * kchunks(K) * kTcTile;
+  if (total == 0) return FNT_RS_OK;
+  k_tc_limbs_a<<<grid_for(p, total), 256, 0, st>>>(A, M, K, kchunks(K), out, total);
+  count_launch();
+  return cuda_ok(cudaGetLastError());
+}
+
+template <class TB>
+int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, const TB* B,
+            size_t ld_b, int W, void* work, uint32_t* out32, size_t row0, uint16_t* out16,
+            const uint32_t* mrow, size_t ld_out, cudaStream_t st) {
+  if (M <= 0 || W <= 0) return FNT_RS_OK;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_fp_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTcSmem) != cudaSuccess)
+      return FNT_RS_E_CUDA;
+    attr = true;
+  }
+  const int K = (int)p->k, Kc = kchunks(K);
+  uint16_t* Bl = static_cast<uint16_t*>(work);
+  const size_t total = (size_t)tiles(W) * Kc * kTcTile;
+  k_tc_limbs_b<TB><<<grid_for(p, total), 256, 0, st>>>(B, ld_b, K, W, Kc, Bl, total, p->status);
+  count_launch();
+  const dim3 grid((unsigned)tiles(W), (unsigned)tiles(M));
+  if (grid.y > 65535u) return FNT_RS_E_ARG;
+  k_fp_gemm_tc<<<grid, 128, kTcSmem, st>>>(Al, Bl, M, Kc, W, corr, out32, row0, out16, mrow,
+                                           ld_out, p->status);
+  count_launch();
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace
 
 bool direct_available(const fnt_rs_plan_s* p) {
   return p->k <= kDirectMaxK && p->n <= kDirectMaxN && p->u == 1;
+}
+
+size_t direct_ws_bytes(const fnt_rs_plan_s* p, size_t W) {
+  if (!p->direct || p->direct->simt || W == 0) return 0;
+  return limb_bytes((int)W, (int)p->k);
 }
 
 void direct_free(fnt_rs_plan_s* p) {
@@ -232,6 +483,8 @@ void direct_free(fnt_rs_plan_s* p) {
   if (!s) return;
   cudaFree(s->G);
   cudaFree(s->D);
+  cudaFree(s->Gl);
+  cudaFree(s->Dl);
   delete s;
   p->direct = nullptr;
 }
@@ -242,6 +495,8 @@ int direct_enable(fnt_rs_plan_s* p) {
   const uint32_t n = p->n, k = p->k;
   DirectState* s = new DirectState();
   p->direct = s;
+  const char* e = std::getenv("FNTRS_DIRECT_SIMT");
+  s->simt = e && e[0] == '1';
   auto fail = [&](int rc) {
     direct_free(p);
     return rc;
@@ -251,38 +506,55 @@ int direct_enable(fnt_rs_plan_s* p) {
   for (uint32_t i = 0; i < k; ++i) xs[i] = hp(r, i);
   for (uint32_t j = k; j < n; ++j) pts[j - k] = hp(r, j);
   lagrange_rows(xs, pts, G);
+  std::vector<uint32_t> gc = centring(G, k);
   int rc;
-  const size_t gbytes = std::max<size_t>(4, G.size() * 4);
-  // G | D (k x k) | mrow (k) | cmap (k uint2)
-  const size_t dwords = (size_t)k * k + k + 2 * (size_t)k;
-  if ((rc = cuda_ok(cudaMalloc(&s->G, gbytes)))) return fail(rc);
+  // G | gcorr, and D | mrow | cmap | dcorr
+  const size_t gwords = std::max<size_t>(1, G.size() + gc.size());
+  const size_t dwords = (size_t)k * k + k + 2 * (size_t)k + k;
+  if ((rc = cuda_ok(cudaMalloc(&s->G, gwords * 4)))) return fail(rc);
+  s->gcorr = s->G + G.size();
   if ((rc = cuda_ok(cudaMalloc(&s->D, dwords * 4)))) return fail(rc);
   s->mrow = s->D + (size_t)k * k;
   s->cmap = reinterpret_cast<uint2*>(s->mrow + k);
+  s->dcorr = s->mrow + 3 * (size_t)k;
   if (!G.empty() &&
-      (rc = cuda_ok(cudaMemcpy(s->G, G.data(), G.size() * 4, cudaMemcpyHostToDevice))))
+      ((rc = cuda_ok(cudaMemcpy(s->G, G.data(), G.size() * 4, cudaMemcpyHostToDevice))) ||
+       (rc = cuda_ok(cudaMemcpy(s->gcorr, gc.data(), gc.size() * 4, cudaMemcpyHostToDevice)))))
     return fail(rc);
+  if (!s->simt) {
+    if ((rc = cuda_ok(cudaMalloc(&s->Gl, std::max<size_t>(16, limb_bytes((int)(n - k), (int)k))))))
+      return fail(rc);
+    if ((rc = cuda_ok(cudaMalloc(&s->Dl, limb_bytes((int)k, (int)k))))) return fail(rc);
+    if ((rc = limbs_a(p, s->G, (int)(n - k), (int)k, s->Gl, nullptr))) return fail(rc);
+    if ((rc = cuda_ok(cudaDeviceSynchronize()))) return fail(rc);
+  }
   return FNT_RS_OK;
 }
 
 int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                      size_t ld_enc, size_t W, cudaStream_t st) {
+                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
   DirectState* s = p->direct;
   if (!s) return FNT_RS_E_ARG;
+  if (!s->simt && !workspace) return FNT_RS_E_WORKSPACE;
   const int k = (int)p->k;
   k_copy_src<<<grid_for(p, (size_t)k * W), 256, 0, st>>>(src, ld_src, enc, ld_enc, k, (int)W);
   count_launch();
   int rc = cuda_ok(cudaGetLastError());
   if (rc) return rc;
-  return launch_gemm<uint16_t>(s->G, (int)(p->n_out - p->k), k, src, ld_src, (int)W, enc,
-                               (size_t)k, nullptr, nullptr, ld_enc, p->status, st);
+  const int M = (int)(p->n_out - p->k);
+  if (s->simt)
+    return launch_gemm<uint16_t>(s->G, M, k, src, ld_src, (int)W, enc, (size_t)k, nullptr,
+                                 nullptr, ld_enc, p->status, st);
+  return gemm_tc<uint16_t>(p, s->Gl, s->gcorr, M, src, ld_src, (int)W, workspace, enc, (size_t)k,
+                           nullptr, nullptr, ld_enc, st);
 }
 
 int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
                       const uint32_t* positions, uint16_t* out, size_t ld_out, size_t W,
-                      cudaStream_t st) {
+                      void* workspace, cudaStream_t st) {
   DirectState* s = p->direct;
   if (!s) return FNT_RS_E_ARG;
+  if (!s->simt && !workspace) return FNT_RS_E_WORKSPACE;
   const uint32_t n = p->n, k = p->k;
   std::vector<uint32_t> key(positions, positions + k);
   if (!s->pattern_ready || s->key != key) {
@@ -304,17 +576,21 @@ int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
         mrow.push_back(m);
       }
     lagrange_rows(xs, pts, D);
+    std::vector<uint32_t> dc = centring(D, k);
     int rc;
-    if (!D.empty() && (rc = cuda_ok(cudaMemcpyAsync(s->D, D.data(), D.size() * 4,
-                                                    cudaMemcpyHostToDevice, st))))
-      return rc;
-    if (!mrow.empty() && (rc = cuda_ok(cudaMemcpyAsync(s->mrow, mrow.data(), mrow.size() * 4,
-                                                       cudaMemcpyHostToDevice, st))))
+    // pageable sources: each copy has staged its data when it returns
+    if (!D.empty() && ((rc = cuda_ok(cudaMemcpyAsync(s->D, D.data(), D.size() * 4,
+                                                     cudaMemcpyHostToDevice, st))) ||
+                       (rc = cuda_ok(cudaMemcpyAsync(s->dcorr, dc.data(), dc.size() * 4,
+                                                     cudaMemcpyHostToDevice, st))) ||
+                       (rc = cuda_ok(cudaMemcpyAsync(s->mrow, mrow.data(), mrow.size() * 4,
+                                                     cudaMemcpyHostToDevice, st)))))
       return rc;
     if (!cmap.empty() && (rc = cuda_ok(cudaMemcpyAsync(s->cmap, cmap.data(), cmap.size() * 8,
                                                        cudaMemcpyHostToDevice, st))))
       return rc;
-    // the host vectors are staged by the copies (pageable memory) before they return
+    if (!s->simt && !D.empty() && (rc = limbs_a(p, s->D, (int)mrow.size(), (int)k, s->Dl, st)))
+      return rc;
     s->nmiss = (int)mrow.size();
     s->ncopy = (int)cmap.size();
     s->key.swap(key);
@@ -328,8 +604,11 @@ int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
     const int rc = cuda_ok(cudaGetLastError());
     if (rc) return rc;
   }
-  return launch_gemm<uint32_t>(s->D, s->nmiss, (int)k, recv, ld_recv, (int)W, nullptr, 0, out,
-                               s->mrow, ld_out, p->status, st);
+  if (s->simt)
+    return launch_gemm<uint32_t>(s->D, s->nmiss, (int)k, recv, ld_recv, (int)W, nullptr, 0, out,
+                                 s->mrow, ld_out, p->status, st);
+  return gemm_tc<uint32_t>(p, s->Dl, s->dcorr, s->nmiss, recv, ld_recv, (int)W, workspace,
+                           nullptr, 0, out, s->mrow, ld_out, st);
 }
 
 }  // namespace fntrs

@@ -189,10 +189,11 @@ int paper_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, 
 bool direct_available(const fnt_rs_plan_s* p);
 int direct_enable(fnt_rs_plan_s* p);
 void direct_free(fnt_rs_plan_s* p);
+size_t direct_ws_bytes(const fnt_rs_plan_s* p, size_t W);
 int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
-                      size_t ld_enc, size_t W, cudaStream_t st);
+                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st);
 int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
                       const uint32_t* positions, uint16_t* out, size_t ld_out, size_t W,
-                      cudaStream_t st);
+                      void* workspace, cudaStream_t st);
 
 }  // namespace fntrs

@@ -94,8 +94,9 @@ bool aligned_to(const void* ptr, size_t a) { return reinterpret_cast<uintptr_t>(
 
 size_t sys_workspace_bytes(const fnt_rs_plan_s* p, size_t W) {
   if (W == 0) return 0;
-  return 2 * align256((size_t)p->n * W * 4) +
-         std::max(dec_ws_max(p, W), fnt_columns_work_bytes(p, W));
+  return std::max(2 * align256((size_t)p->n * W * 4) +
+                      std::max(dec_ws_max(p, W), fnt_columns_work_bytes(p, W)),
+                  direct_ws_bytes(p, W));
 }
 
 }  // namespace fntrs
@@ -118,7 +119,7 @@ int fnt_rs_encode_sys(fnt_rs_plan p, const uint16_t* src, size_t ld_src, uint32_
   if (p->u != 1) return FNT_RS_E_ROOT;  // positions 0..k-1 are those of the default root
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (p->sched_sys_enc == FNT_RS_SCHED_DIRECT)
-    return direct_encode_sys(p, src, ld_src, enc, ld_enc, W, st);
+    return direct_encode_sys(p, src, ld_src, enc, ld_enc, W, workspace, st);
   if (!workspace) return FNT_RS_E_WORKSPACE;
   const size_t n = p->n, k = p->k;
   const SysWs w = sys_split(p, W, workspace);
@@ -158,7 +159,7 @@ int fnt_rs_decode_sys(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv,
     return cuda_ok(cudaGetLastError());
   }
   if (p->sched_sys_dec == FNT_RS_SCHED_DIRECT)
-    return direct_decode_sys(p, recv, ld_recv, positions, out, ld_out, W, st);
+    return direct_decode_sys(p, recv, ld_recv, positions, out, ld_out, W, workspace, st);
   if (!workspace) return FNT_RS_E_WORKSPACE;
   const SysWs w = sys_split(p, W, workspace);
   if (n > k && (rc = cuda_ok(cudaMemsetAsync(w.Z + k * W, 0, (n - k) * W * 4, st)))) return rc;

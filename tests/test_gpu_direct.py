@@ -101,3 +101,22 @@ def test_direct_availability_and_switch_back(pkg):
     src = synth.source(9, 100, 12)
     assert np.array_equal(pkg.to_host(plan.encode_sys(pkg.to_device(src))),
                           oracle.encode_sys(src, 256))
+
+
+def test_tensor_core_and_integer_products_agree(pkg, monkeypatch):
+    """The direct methods run their matrix products on the tensor cores (BF16 limbs,
+    exact FP32 accumulation); FNTRS_DIRECT_SIMT=1 selects the integer kernel.  Both
+    must give the oracle's words, at the largest k the exactness bound allows."""
+    n, k, W = 2048, 1024, 136
+    src = synth.source(77, k, W)
+    want = oracle.encode_sys(src, n)
+    pos = synth.received_positions(n, synth.erased_uniform(78, n, k))
+    v = synth.received_uniform(79, k, W)
+    want_d, _ = oracle.decode_sys(v, pos, n, k)
+    for simt in ("0", "1"):
+        monkeypatch.setenv("FNTRS_DIRECT_SIMT", simt)
+        plan = _direct_plan(pkg, n, k)
+        assert np.array_equal(pkg.to_host(plan.encode_sys(pkg.to_device(src))), want), simt
+        got = pkg.to_host(plan.decode_sys(pkg.to_device(v), pos))
+        assert np.array_equal(got, want_d), simt
+        plan.status()
