@@ -175,15 +175,20 @@ __global__ void __launch_bounds__(256) k_fp_gemm(const uint32_t* __restrict__ A,
 }
 
 // ---- tensor-core product ---------------------------------------------------
-// Operand tiles of 128 rows x 64 K-values, K-major core-matrix layout (8 rows
-// x 8 values = 128 bytes per core matrix, 128 bytes apart along K, 1024 bytes
-// apart along the rows), the two limbs of a tile 16 KB apart: the global image
-// of one (row tile, K chunk) pair is exactly the 32 KB its shared-memory stage
-// holds.
-constexpr int kTcRows = 128, kTcK = 64, kTcTile = kTcRows * kTcK;  // elements per limb tile
-constexpr int kTcChunkBytes = 2 * kTcTile * 2;                     // both limbs, bf16
-constexpr int kTcSmem = 120 * 1024;  // more than half an SM: one CTA (and one TMEM user) per SM
-constexpr uint32_t kTcIdesc = idesc_bf16_f32<128, 128>();
+// Operand tiles of R rows x 64 K-values in the K-major core-matrix layout
+// (8 rows x 8 values = 128 bytes per core matrix, 128 bytes apart along K,
+// 1024 bytes apart along the rows), the two limbs of a tile one tile apart:
+// the global image of one (row tile, K chunk) pair is exactly what its
+// shared-memory stage holds, so one bulk copy moves it.  A (the matrix) has
+// 128-row tiles, B (the data, as the N x K operand) 64-row tiles.
+constexpr int kTcRows = 128, kTcN = 64, kTcK = 64;
+constexpr int kTcTile = kTcRows * kTcK, kTcBTile = kTcN * kTcK;  // elements per limb tile
+constexpr int kTcABytes = 2 * kTcTile * 2, kTcBBytes = 2 * kTcBTile * 2;  // both limbs, bf16
+constexpr int kTcStages = 4;
+constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;  // one CTA (one TMEM user) per SM
+constexpr uint32_t kTcCols = 4 * kTcN;                      // four FP32 accumulators
+constexpr uint32_t kTcIdesc = idesc_bf16_f32<128, kTcN>();
 
 __device__ __forceinline__ int tc_off(int r, int k) {
   return (r >> 3) * 512 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
@@ -224,36 +229,42 @@ __global__ void k_tc_limbs_a(const uint32_t* __restrict__ A, int M, int K, int K
 
 // limb tiles of the data B [K][ld_b] seen as the N x K operand (row n = column
 // n of B), centred: x - 32768 with x = value mod p (received values above
-// 65536 raise the range flag)
+// 65536 raise the range flag); tile (nt, kc) at ((nt * Kc + kc) * 2 + limb) * kTcBTile
+// With `copy` set, B is also copied there as u32 rows (the systematic rows of
+// an encode, read once for both).
 template <class TB>
 __global__ void k_tc_limbs_b(const TB* __restrict__ B, size_t ld_b, int K, int W, int Kc,
-                             uint16_t* __restrict__ out, size_t total, int* status) {
+                             uint16_t* __restrict__ out, size_t total, int* status,
+                             uint32_t* __restrict__ copy, size_t ld_copy) {
   bool bad = false;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const size_t tile = t / kTcTile;
-    const int e = (int)(t % kTcTile), kk = e / kTcRows, r = e % kTcRows;  // r fastest: coalesced
+    const size_t tile = t / kTcBTile;
+    const int e = (int)(t % kTcBTile), kk = e / kTcN, r = e % kTcN;  // r fastest: coalesced
     const int nt = (int)(tile / Kc), kc = (int)(tile % Kc);
-    const int n = nt * kTcRows + r, k = kc * kTcK + kk;
+    const int n = nt * kTcN + r, k = kc * kTcK + kk;
     int v = 0;
     if (n < W && k < K) {
       const uint32_t x = (uint32_t)B[(size_t)k * ld_b + n];
       bad |= x > 65536u;
       v = (int)m_to_p(x) - 32768;
+      if (copy) copy[(size_t)k * ld_copy + n] = x;
     }
     int lo, hi;
     split_limbs(v, lo, hi);
-    uint16_t* o = out + tile * 2 * kTcTile + tc_off(r, kk);
+    uint16_t* o = out + tile * 2 * kTcBTile + tc_off(r, kk);
     o[0] = bf16_bits(lo);
-    o[kTcTile] = bf16_bits(hi);
+    o[kTcBTile] = bf16_bits(hi);
   }
   if (bad) atomicOr(status, ST_RANGE);
 }
 
-// C = A B over F_p for one 128 x 128 output tile: K in chunks of 64, each
-// chunk's limb tiles staged in shared memory and multiplied by one thread
-// issuing 4 K-steps x 4 limb pairs of 128x128x16 BF16 MMAs into four FP32
-// accumulators (all 512 tensor-memory columns).  Output as in k_fp_gemm.
+// C = A B over F_p for one 128 x 64 output tile.  Thread 0 keeps up to
+// kTcStages K chunks in flight (one bulk copy of the A chunk and one of the B
+// chunk per stage, completing on the stage's `full` barrier) and, per chunk,
+// issues 4 K-steps x 4 limb pairs of 128x64x16 BF16 MMAs into four FP32
+// accumulators, whose completion (tcgen05.commit) frees the stage.  All waits
+// are bounded.  Output as in k_fp_gemm.
 __global__ void __launch_bounds__(128, 1)
     k_fp_gemm_tc(const uint16_t* __restrict__ Al, const uint16_t* __restrict__ Bl, int M, int Kc,
                  int W, const uint32_t* __restrict__ corr, uint32_t* __restrict__ out32,
@@ -262,90 +273,123 @@ __global__ void __launch_bounds__(128, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint16_t* sA = reinterpret_cast<uint16_t*>(base);
-  uint16_t* sB = reinterpret_cast<uint16_t*>(base + kTcChunkBytes);
-  __shared__ uint64_t bar;
+  __shared__ uint64_t full[kTcStages], empty[kTcStages];
   __shared__ uint32_t tslot;
+  __shared__ int s_ok;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mt = blockIdx.y, nt = blockIdx.x;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  if (warp == 0) tmem_alloc(&tslot, 512);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    s_ok = 1;
+  }
+  if (warp == 0) tmem_alloc(&tslot, kTcCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = tslot;
-  const uint4* gA = reinterpret_cast<const uint4*>(Al + (size_t)mt * Kc * 2 * kTcTile);
-  const uint4* gB = reinterpret_cast<const uint4*>(Bl + (size_t)nt * Kc * 2 * kTcTile);
-  constexpr int kVec = kTcChunkBytes / 16;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int c = 0; c < Kc && ok; ++c) {
-    const uint4* a = gA + (size_t)c * kVec;
-    const uint4* b = gB + (size_t)c * kVec;
-    for (int i = threadIdx.x; i < kVec; i += 128) {
-      reinterpret_cast<uint4*>(sA)[i] = __ldg(a + i);
-      reinterpret_cast<uint4*>(sB)[i] = __ldg(b + i);
-    }
-    fence_proxy_async();  // the tensor cores read shared memory through the async proxy
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    const uint8_t* gA = reinterpret_cast<const uint8_t*>(Al) + (size_t)mt * Kc * kTcABytes;
+    const uint8_t* gB = reinterpret_cast<const uint8_t*>(Bl) + (size_t)nt * Kc * kTcBBytes;
+    auto load = [&](int c) {
+      uint8_t* st = base + (c % kTcStages) * kTcStageBytes;
+      uint64_t* bar = &full[c % kTcStages];
+      mbar_expect_tx(bar, kTcStageBytes);
+      bulk_g2s(st, gA + (size_t)c * kTcABytes, kTcABytes, bar);
+      bulk_g2s(st + kTcABytes, gB + (size_t)c * kTcBBytes, kTcBBytes, bar);
+    };
+    const int pre = Kc < kTcStages ? Kc : kTcStages;
+    for (int c = 0; c < pre; ++c) load(c);
+    int loaded = pre, issued = 0;
+    bool ok = true;
+    for (int c = 0; c < Kc; ++c) {
+      const int s = c % kTcStages;
+      const uint32_t ph = (uint32_t)(c / kTcStages) & 1u;
+      if (!(ok = mbar_wait(&full[s], ph))) break;
       tc_fence_after();
+      const uint16_t* sA = reinterpret_cast<const uint16_t*>(base + s * kTcStageBytes);
+      const uint16_t* sB = reinterpret_cast<const uint16_t*>(base + s * kTcStageBytes + kTcABytes);
 #pragma unroll
-      for (int s = 0; s < kTcK / 16; ++s)
+      for (int k = 0; k < kTcK / 16; ++k)
 #pragma unroll
         for (int la = 0; la < 2; ++la)
 #pragma unroll
-          for (int lb = 0; lb < 2; ++lb) {
-            const uint64_t ad = smem_desc(sA + la * kTcTile + s * 128, 128, 1024);
-            const uint64_t bd = smem_desc(sB + lb * kTcTile + s * 128, 128, 1024);
-            mma_bf16(taddr + (uint32_t)(2 * la + lb) * 128u, ad, bd, kTcIdesc,
-                     (c > 0 || s > 0) ? 1u : 0u);
-          }
-      mma_commit(&bar);
+          for (int lb = 0; lb < 2; ++lb)
+            mma_bf16(taddr + (uint32_t)(2 * la + lb) * kTcN,
+                     smem_desc(sA + la * kTcTile + k * 128, 128, 1024),
+                     smem_desc(sB + lb * kTcBTile + k * 128, 128, 1024), kTcIdesc,
+                     (c > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+      issued = c + 1;
+      if (c + kTcStages < Kc) {
+        // the stage is refilled once its MMAs are done; the other stages stay in flight
+        if (!(ok = mbar_wait(&empty[s], ph))) break;
+        load(c + kTcStages);
+        loaded = c + kTcStages + 1;
+      }
     }
-    // the stage is refilled (and the accumulators read) only after the MMAs finish
-    ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
-    ok = !__syncthreads_or(!ok);
+    if (ok && issued > 0) {  // the last commit covers every MMA issued before it
+      const int c = issued - 1;
+      ok = mbar_wait(&empty[c % kTcStages], (uint32_t)(c / kTcStages) & 1u);
+    }
+    if (!ok) {
+      atomicOr(status, ST_TIMEOUT);
+      // bounded waits for the copies and MMAs still in flight before TMEM is freed
+      for (int c = issued; c < loaded; ++c)
+        mbar_wait(&full[c % kTcStages], (uint32_t)(c / kTcStages) & 1u);
+      if (issued > 0)
+        mbar_wait(&empty[(issued - 1) % kTcStages], (uint32_t)((issued - 1) / kTcStages) & 1u);
+      s_ok = 0;
+    }
   }
-  if (ok) {
+  __syncthreads();
+  if (s_ok) {
+    // each thread combines its accumulator row into a [128][65] tile in the
+    // (now free) stage memory; the tile then leaves in whole rows
+    uint32_t* tile = reinterpret_cast<uint32_t*>(base);
     tc_fence_after();
-    const int r = mt * kTcRows + warp * 32 + lane;
+    const int rl = warp * 32 + lane;
+    const int r = mt * kTcRows + rl;
     const uint32_t lane_addr = taddr + ((uint32_t)(warp * 32) << 16);
-    const int64_t cr = r < M ? (int64_t)corr[r] : 0;
-    bool bad = false;
-    for (int j0 = 0; j0 < kTcRows; j0 += 16) {
+    // |value| < 2^34 + 2^17 < 65537 * 2^18: adding that multiple of p makes it positive
+    const int64_t bias = (r < M ? (int64_t)corr[r] : 0) + 65537ll * (1ll << 18);
+    for (int j0 = 0; j0 < kTcN; j0 += 16) {
       float c00[16], c01[16], c10[16], c11[16];
-      tmem_ld16(lane_addr + 0u * 128u + (uint32_t)j0, c00);
-      tmem_ld16(lane_addr + 1u * 128u + (uint32_t)j0, c01);
-      tmem_ld16(lane_addr + 2u * 128u + (uint32_t)j0, c10);
-      tmem_ld16(lane_addr + 3u * 128u + (uint32_t)j0, c11);
-      if (r >= M) continue;
+      tmem_ld16(lane_addr + 0u * kTcN + (uint32_t)j0, c00);
+      tmem_ld16(lane_addr + 1u * kTcN + (uint32_t)j0, c01);
+      tmem_ld16(lane_addr + 2u * kTcN + (uint32_t)j0, c10);
+      tmem_ld16(lane_addr + 3u * kTcN + (uint32_t)j0, c11);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int col = nt * kTcRows + j0 + i;
-        if (col >= W) continue;
-        int64_t v = (int64_t)__float2int_rn(c00[i]) +
-                    256 * ((int64_t)__float2int_rn(c01[i]) + (int64_t)__float2int_rn(c10[i])) -
-                    (int64_t)__float2int_rn(c11[i]) + cr;
-        v %= 65537;
-        if (v < 0) v += 65537;
-        if (out32) {
-          out32[(row0 + r) * ld_out + col] = (uint32_t)v;
-        } else {
-          bad |= v > 65535;
-          out16[(size_t)mrow[r] * ld_out + col] = (uint16_t)(v > 65535 ? 0 : v);
-        }
+        const uint64_t u = (uint64_t)((int64_t)__float2int_rn(c00[i]) +
+                                      256 * ((int64_t)__float2int_rn(c01[i]) +
+                                             (int64_t)__float2int_rn(c10[i])) -
+                                      (int64_t)__float2int_rn(c11[i]) + bias);
+        // 2^32 = 1 mod p: fold the high word, then reduce
+        tile[rl * (kTcN + 1) + j0 + i] = m_to_p(m_add((uint32_t)u, (uint32_t)(u >> 32)));
+      }
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int e = threadIdx.x; e < kTcRows * kTcN; e += 128) {
+      const int rr = e / kTcN, j = e % kTcN;
+      const int row = mt * kTcRows + rr, col = nt * kTcN + j;
+      if (row >= M || col >= W) continue;
+      const uint32_t v = tile[rr * (kTcN + 1) + j];
+      if (out32) {
+        out32[(row0 + row) * ld_out + col] = v;
+      } else {
+        bad |= v > 65535u;
+        out16[(size_t)mrow[row] * ld_out + col] = (uint16_t)(v > 65535u ? 0u : v);
       }
     }
     if (bad) atomicOr(status, ST_RANGE);
-  } else if (threadIdx.x == 0) {
-    atomicOr(status, ST_TIMEOUT);
-    mbar_wait(&bar, phase ^ 1u);  // bounded: let MMAs still in flight finish
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, 512);
+  if (warp == 0) tmem_dealloc(taddr, kTcCols);
 }
 
 // encode: enc[i][c] = src[i][c], i < k
@@ -419,8 +463,10 @@ struct DirectState {
 namespace {
 
 int tiles(int rows) { return (rows + kTcRows - 1) / kTcRows; }
+int ntiles(int cols) { return (cols + kTcN - 1) / kTcN; }
 int kchunks(int K) { return (K + kTcK - 1) / kTcK; }
-size_t limb_bytes(int rows, int K) { return (size_t)tiles(rows) * kchunks(K) * kTcChunkBytes; }
+size_t limb_bytes(int rows, int K) { return (size_t)tiles(rows) * kchunks(K) * kTcABytes; }
+size_t data_limb_bytes(int cols, int K) { return (size_t)ntiles(cols) * kchunks(K) * kTcBBytes; }
 
 std::vector<uint32_t> centring(const std::vector<uint32_t>& rows, size_t k) {
   const size_t m = k ? rows.size() / k : 0;
@@ -445,8 +491,10 @@ int limbs_a(const fnt_rs_plan_s* p, const uint32_t* A, int M, int K, uint16_t* o
 template <class TB>
 int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, const TB* B,
             size_t ld_b, int W, void* work, uint32_t* out32, size_t row0, uint16_t* out16,
-            const uint32_t* mrow, size_t ld_out, cudaStream_t st) {
-  if (M <= 0 || W <= 0) return FNT_RS_OK;
+            const uint32_t* mrow, size_t ld_out, cudaStream_t st, uint32_t* copy = nullptr,
+            size_t ld_copy = 0) {
+  if (W <= 0 || (M <= 0 && !copy)) return FNT_RS_OK;
+  if (reinterpret_cast<uintptr_t>(work) % 16 != 0) return FNT_RS_E_ARG;  // bulk-copy source
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_fp_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -456,10 +504,12 @@ int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, c
   }
   const int K = (int)p->k, Kc = kchunks(K);
   uint16_t* Bl = static_cast<uint16_t*>(work);
-  const size_t total = (size_t)tiles(W) * Kc * kTcTile;
-  k_tc_limbs_b<TB><<<grid_for(p, total), 256, 0, st>>>(B, ld_b, K, W, Kc, Bl, total, p->status);
+  const size_t total = (size_t)ntiles(W) * Kc * kTcBTile;
+  k_tc_limbs_b<TB><<<grid_for(p, total), 256, 0, st>>>(B, ld_b, K, W, Kc, Bl, total, p->status,
+                                                        copy, ld_copy);
   count_launch();
-  const dim3 grid((unsigned)tiles(W), (unsigned)tiles(M));
+  if (M <= 0) return cuda_ok(cudaGetLastError());
+  const dim3 grid((unsigned)ntiles(W), (unsigned)tiles(M));
   if (grid.y > 65535u) return FNT_RS_E_ARG;
   k_fp_gemm_tc<<<grid, 128, kTcSmem, st>>>(Al, Bl, M, Kc, W, corr, out32, row0, out16, mrow,
                                            ld_out, p->status);
@@ -475,7 +525,7 @@ bool direct_available(const fnt_rs_plan_s* p) {
 
 size_t direct_ws_bytes(const fnt_rs_plan_s* p, size_t W) {
   if (!p->direct || p->direct->simt || W == 0) return 0;
-  return limb_bytes((int)W, (int)p->k);
+  return data_limb_bytes((int)W, (int)p->k);
 }
 
 void direct_free(fnt_rs_plan_s* p) {
@@ -537,16 +587,16 @@ int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   if (!s) return FNT_RS_E_ARG;
   if (!s->simt && !workspace) return FNT_RS_E_WORKSPACE;
   const int k = (int)p->k;
+  const int M = (int)(p->n_out - p->k);
+  if (!s->simt)  // the systematic rows are copied by the kernel that splits the source
+    return gemm_tc<uint16_t>(p, s->Gl, s->gcorr, M, src, ld_src, (int)W, workspace, enc,
+                             (size_t)k, nullptr, nullptr, ld_enc, st, enc, ld_enc);
   k_copy_src<<<grid_for(p, (size_t)k * W), 256, 0, st>>>(src, ld_src, enc, ld_enc, k, (int)W);
   count_launch();
-  int rc = cuda_ok(cudaGetLastError());
+  const int rc = cuda_ok(cudaGetLastError());
   if (rc) return rc;
-  const int M = (int)(p->n_out - p->k);
-  if (s->simt)
-    return launch_gemm<uint16_t>(s->G, M, k, src, ld_src, (int)W, enc, (size_t)k, nullptr,
-                                 nullptr, ld_enc, p->status, st);
-  return gemm_tc<uint16_t>(p, s->Gl, s->gcorr, M, src, ld_src, (int)W, workspace, enc, (size_t)k,
-                           nullptr, nullptr, ld_enc, st);
+  return launch_gemm<uint16_t>(s->G, M, k, src, ld_src, (int)W, enc, (size_t)k, nullptr, nullptr,
+                               ld_enc, p->status, st);
 }
 
 int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,

@@ -9,6 +9,17 @@
 
 namespace fntrs {
 
+// 1-D bulk copy (TMA engine) of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Columns of tensor memory allocated by one warp (power of two, 32..512); the
 // address of the allocation is written to shared memory at `slot`.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
