@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/fnt_rs.h"
@@ -52,8 +53,21 @@ struct Chunking {
   size_t w;
 };
 
+// FNTRS_HOST_CHUNKS (1..8) overrides the chunk count cap (for measurements)
+int chunks_max() {
+  static const int v = [] {
+    const char* e = std::getenv("FNTRS_HOST_CHUNKS");
+    const int x = e ? std::atoi(e) : 0;
+    return x >= 1 && x <= kPipeChunks ? x : kChunksMax;
+  }();
+  return v;
+}
+
 Chunking chunking(size_t W) {
-  const int want = (int)std::min<size_t>(kChunksMax, std::max<size_t>(1, W / kChunkMin));
+  const int want = (int)std::min<size_t>((size_t)chunks_max(),
+                                         std::max<size_t>(1, W / (chunks_max() > kChunksMax
+                                                                      ? kChunkMin / 2
+                                                                      : kChunkMin)));
   size_t w = (W + want - 1) / want;
   w = (w + 63) / 64 * 64;  // chunk starts stay 128-byte aligned
   return Chunking{(int)((W + w - 1) / w), w};
