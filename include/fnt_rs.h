@@ -132,7 +132,17 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *                       k <= n/2, default root).  Selecting it builds its
  *                       tables (synchronising the device) and grows the
  *                       decode workspace by 2 * 2n * W * 4 bytes (query the
- *                       size after selecting it); the autotuner never picks it.
+ *                       size after selecting it); the autotuner never picks it,
+ *   FNT_RS_SCHED_DIRECT the quadratic method (Sec. III) as one matrix product
+ *                       over F_p per batch on the tensor cores (k <= 1024,
+ *                       n <= 16384, default root): encode by the n x k matrix
+ *                       r^(ij); decode by the k x k matrix of the Lagrange
+ *                       basis coefficients of the first k positions (built on
+ *                       the host once per erasure pattern).  Selecting it
+ *                       builds the plan-level matrix (synchronising the
+ *                       device); the workspace covers it once selected.  A
+ *                       16-bit wire encode (fnt_rs_encode_wire) keeps the
+ *                       transform schedules.
  * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else TILE
  * (encode up to n = 8192; decode wherever one CTA holds the codeword), else
  * SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
@@ -169,8 +179,9 @@ int fnt_rs_set_schedule(fnt_rs_plan plan, int op, int sched);
 int fnt_rs_get_schedule(fnt_rs_plan plan, int op);
 
 /*
- * Autotuner.  Runs every schedule of `op` that can run this plan on W
- * codewords of zeroed data (at most 2^29 bytes of encoded words: a larger W
+ * Autotuner.  Runs every schedule of `op` that can run this plan (but
+ * FNT_RS_SCHED_PAPER; FNT_RS_SCHED_DIRECT included, whose matrices it builds
+ * and keeps in the plan) on W codewords of zeroed data (at most 2^29 bytes of encoded words: a larger W
  * is timed on fewer columns, a multiple of 8) in device buffers it allocates
  * and frees itself, times each with CUDA events on `stream` (median of 5
  * calls after 2 warm-up calls; the time of an integer transform does not

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) k_fp_gemm(const uint32_t* __restrict__ A,
                                                  uint32_t* __restrict__ out32, size_t row0,
                                                  uint16_t* __restrict__ out16,
                                                  const uint32_t* __restrict__ mrow, size_t ld_out,
-                                                 int* status) {
+                                                 int* status, const uint32_t* __restrict__ rmap) {
   constexpr int TM = 64, TN = 64, TK = 32;
   __shared__ uint32_t As[TK][TM + 1];
   __shared__ uint32_t Bs[TK][TN];
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256) k_fp_gemm(const uint32_t* __restrict__ A,
       const int t = e / TN, c = e % TN;
       uint32_t v = 0;
       if (k0 + t < K && c0 + c < W) {
-        v = (uint32_t)B[(size_t)(k0 + t) * ld_b + c0 + c];
+        const size_t row = rmap ? (size_t)rmap[k0 + t] : (size_t)(k0 + t);
+        v = (uint32_t)B[row * ld_b + c0 + c];
         bad |= v > 65536u;
       }
       Bs[t][c] = v;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256) k_fp_gemm(const uint32_t* __restrict__ A,
         out32[(row0 + r) * ld_out + c] = v;
       } else {
         bad |= v > 65535u;
-        out16[(size_t)mrow[r] * ld_out + c] = (uint16_t)(v > 65535u ? 0u : v);
+        out16[(mrow ? (size_t)mrow[r] : (size_t)r) * ld_out + c] = (uint16_t)(v > 65535u ? 0u : v);
       }
     }
   }
@@ -232,10 +233,12 @@ __global__ void k_tc_limbs_a(const uint32_t* __restrict__ A, int M, int K, int K
 // 65536 raise the range flag); tile (nt, kc) at ((nt * Kc + kc) * 2 + limb) * kTcBTile
 // With `copy` set, B is also copied there as u32 rows (the systematic rows of
 // an encode, read once for both).
+// With `rmap` set, row k of the operand is row rmap[k] of B.
 template <class TB>
 __global__ void k_tc_limbs_b(const TB* __restrict__ B, size_t ld_b, int K, int W, int Kc,
                              uint16_t* __restrict__ out, size_t total, int* status,
-                             uint32_t* __restrict__ copy, size_t ld_copy) {
+                             uint32_t* __restrict__ copy, size_t ld_copy,
+                             const uint32_t* __restrict__ rmap) {
   bool bad = false;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -245,7 +248,8 @@ __global__ void k_tc_limbs_b(const TB* __restrict__ B, size_t ld_b, int K, int W
     const int n = nt * kTcN + r, k = kc * kTcK + kk;
     int v = 0;
     if (n < W && k < K) {
-      const uint32_t x = (uint32_t)B[(size_t)k * ld_b + n];
+      const size_t row = rmap ? (size_t)rmap[k] : (size_t)k;
+      const uint32_t x = (uint32_t)B[row * ld_b + n];
       bad |= x > 65536u;
       v = (int)m_to_p(x) - 32768;
       if (copy) copy[(size_t)k * ld_copy + n] = x;
@@ -382,7 +386,8 @@ __global__ void __launch_bounds__(128, 1)
         out32[(row0 + row) * ld_out + col] = v;
       } else {
         bad |= v > 65535u;
-        out16[(size_t)mrow[row] * ld_out + col] = (uint16_t)(v > 65535u ? 0u : v);
+        out16[(mrow ? (size_t)mrow[row] : (size_t)row) * ld_out + col] =
+            (uint16_t)(v > 65535u ? 0u : v);
       }
     }
     if (bad) atomicOr(status, ST_RANGE);
@@ -430,12 +435,12 @@ unsigned grid_for(const fnt_rs_plan_s* p, size_t work) {
 template <class TB>
 int launch_gemm(const uint32_t* A, int M, int K, const TB* B, size_t ld_b, int W, uint32_t* out32,
                 size_t row0, uint16_t* out16, const uint32_t* mrow, size_t ld_out, int* status,
-                cudaStream_t st) {
+                cudaStream_t st, const uint32_t* rmap = nullptr) {
   if (M <= 0 || W <= 0) return FNT_RS_OK;
   const dim3 grid((unsigned)((W + 63) / 64), (unsigned)((M + 63) / 64));
   if (grid.y > 65535u) return FNT_RS_E_ARG;
   k_fp_gemm<TB><<<grid, 256, 0, st>>>(A, M, K, B, ld_b, W, out32, row0, out16, mrow, ld_out,
-                                      status);
+                                      status, rmap);
   count_launch();
   return cuda_ok(cudaGetLastError());
 }
@@ -445,19 +450,34 @@ int launch_gemm(const uint32_t* A, int M, int K, const TB* B, size_t ld_b, int W
 constexpr uint32_t kDirectMaxK = 1024;  // also the exactness bound of the tensor-core product
 constexpr uint32_t kDirectMaxN = 16384;
 
+// One matrix of a direct product: u32 entries in [0, p) (the integer kernel's
+// operand and the source of the limb tiles), the tensor-core limb tiles and
+// the per-row centring correction 32768 * row sum.
+struct DirectMat {
+  uint32_t* a = nullptr;
+  uint32_t* corr = nullptr;
+  uint16_t* limbs = nullptr;
+  int rows = 0;
+};
+
 struct DirectState {
-  uint32_t* G = nullptr;     // [(n - k)][k]: L_i(r^j), j = k .. n-1
-  uint32_t* D = nullptr;     // [k][k] max: rows of the missing source symbols
-  uint32_t* mrow = nullptr;  // [k]: output row of each D row
-  uint2* cmap = nullptr;     // [k]: {received row, output row} of received source rows
-  uint32_t* gcorr = nullptr; // [n - k]: 32768 * row sum of G (the data centring), mod p
-  uint32_t* dcorr = nullptr; // [k]: the same for D
-  uint16_t* Gl = nullptr;    // limb tiles of G (tensor-core product)
-  uint16_t* Dl = nullptr;    // limb tiles of D
-  std::vector<uint32_t> key;
+  bool simt = false;  // FNTRS_DIRECT_SIMT=1: the integer kernel instead of the tensor cores
+  // systematic encode: G [(n - k)][k] = L_i(r^j), j = k .. n-1 (built when selected)
+  DirectMat G;
+  // non-systematic encode: V [n][k] = r^(ij) (built when selected)
+  DirectMat V;
+  // systematic decode, per pattern: D [missing][k], its output rows and the copies
+  DirectMat D;
+  uint32_t* mrow = nullptr;  // [k]
+  uint2* cmap = nullptr;     // [k]: {received row, output row}
+  std::vector<uint32_t> dkey;
   int nmiss = 0, ncopy = 0;
-  bool pattern_ready = false;
-  bool simt = false;         // FNTRS_DIRECT_SIMT=1: the integer kernel instead
+  bool d_ready = false;
+  // non-systematic decode, per pattern: M [k][k] = coefficients of the Lagrange basis
+  DirectMat Mi;
+  uint32_t* rmap = nullptr;  // [k]: slot-buffer row of basis index l (= its position)
+  std::vector<uint32_t> mkey;
+  bool m_ready = false;
 };
 
 namespace {
@@ -488,11 +508,42 @@ int limbs_a(const fnt_rs_plan_s* p, const uint32_t* A, int M, int K, uint16_t* o
   return cuda_ok(cudaGetLastError());
 }
 
+void mat_free(DirectMat& m) {
+  cudaFree(m.a);
+  cudaFree(m.limbs);
+  m = DirectMat{};
+}
+
+// device storage for up to `rows` x k entries (+ limbs unless simt)
+int mat_alloc(DirectMat& m, int rows, int k, bool simt) {
+  if (m.a) return FNT_RS_OK;
+  int rc = cuda_ok(cudaMalloc(&m.a, ((size_t)std::max(rows, 1) * k + std::max(rows, 1)) * 4));
+  if (rc) return rc;
+  m.corr = m.a + (size_t)std::max(rows, 1) * k;
+  if (!simt && (rc = cuda_ok(cudaMalloc(&m.limbs, std::max<size_t>(16, limb_bytes(rows, k))))))
+    return rc;
+  return FNT_RS_OK;
+}
+
+// host matrix -> device entries, corrections and limb tiles (on st; the host
+// vectors are staged by the pageable copies before they return)
+int mat_upload(const fnt_rs_plan_s* p, DirectMat& m, const std::vector<uint32_t>& a, int rows,
+               int k, bool simt, cudaStream_t st) {
+  m.rows = rows;
+  if (rows == 0) return FNT_RS_OK;
+  const std::vector<uint32_t> c = centring(a, (size_t)k);
+  int rc = cuda_ok(cudaMemcpyAsync(m.a, a.data(), a.size() * 4, cudaMemcpyHostToDevice, st));
+  if (!rc)
+    rc = cuda_ok(cudaMemcpyAsync(m.corr, c.data(), c.size() * 4, cudaMemcpyHostToDevice, st));
+  if (!rc && !simt) rc = limbs_a(p, m.a, rows, k, m.limbs, st);
+  return rc;
+}
+
 template <class TB>
 int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, const TB* B,
             size_t ld_b, int W, void* work, uint32_t* out32, size_t row0, uint16_t* out16,
             const uint32_t* mrow, size_t ld_out, cudaStream_t st, uint32_t* copy = nullptr,
-            size_t ld_copy = 0) {
+            size_t ld_copy = 0, const uint32_t* rmap = nullptr) {
   if (W <= 0 || (M <= 0 && !copy)) return FNT_RS_OK;
   if (reinterpret_cast<uintptr_t>(work) % 16 != 0) return FNT_RS_E_ARG;  // bulk-copy source
   static bool attr = false;
@@ -506,7 +557,7 @@ int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, c
   uint16_t* Bl = static_cast<uint16_t*>(work);
   const size_t total = (size_t)ntiles(W) * Kc * kTcBTile;
   k_tc_limbs_b<TB><<<grid_for(p, total), 256, 0, st>>>(B, ld_b, K, W, Kc, Bl, total, p->status,
-                                                        copy, ld_copy);
+                                                        copy, ld_copy, rmap);
   count_launch();
   if (M <= 0) return cuda_ok(cudaGetLastError());
   const dim3 grid((unsigned)ntiles(W), (unsigned)tiles(M));
@@ -517,6 +568,22 @@ int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, c
   return cuda_ok(cudaGetLastError());
 }
 
+// C = A B with A one of the direct matrices (rows m.rows), on the tensor cores
+// or (systematic ops with FNTRS_DIRECT_SIMT=1) the integer kernel, which must
+// not write the rows it reads
+template <class TB>
+int product(fnt_rs_plan_s* p, const DirectMat& m, const TB* B, size_t ld_b, int W, void* work,
+            uint32_t* out32, size_t row0, uint16_t* out16, const uint32_t* mrow, size_t ld_out,
+            cudaStream_t st, bool simt, const uint32_t* rmap = nullptr) {
+  if (simt)
+    return launch_gemm<TB>(m.a, m.rows, (int)p->k, B, ld_b, W, out32, row0, out16, mrow, ld_out,
+                           p->status, st, rmap);
+  return gemm_tc<TB>(p, m.limbs, m.corr, m.rows, B, ld_b, W, work, out32, row0, out16, mrow,
+                     ld_out, st, nullptr, 0, rmap);
+}
+
+uint32_t root_of(uint32_t n) { return hp(3, 65536u / n); }
+
 }  // namespace
 
 bool direct_available(const fnt_rs_plan_s* p) {
@@ -524,92 +591,108 @@ bool direct_available(const fnt_rs_plan_s* p) {
 }
 
 size_t direct_ws_bytes(const fnt_rs_plan_s* p, size_t W) {
-  if (!p->direct || p->direct->simt || W == 0) return 0;
+  if (!p->direct || W == 0) return 0;
   return data_limb_bytes((int)W, (int)p->k);
 }
 
 void direct_free(fnt_rs_plan_s* p) {
   DirectState* s = p->direct;
   if (!s) return;
-  cudaFree(s->G);
-  cudaFree(s->D);
-  cudaFree(s->Gl);
-  cudaFree(s->Dl);
+  mat_free(s->G);
+  mat_free(s->V);
+  mat_free(s->D);
+  mat_free(s->Mi);
+  cudaFree(s->mrow);
+  cudaFree(s->rmap);
   delete s;
   p->direct = nullptr;
 }
 
-int direct_enable(fnt_rs_plan_s* p) {
-  if (p->direct) return FNT_RS_OK;
+// Builds what the direct method of `op` needs (FNT_RS_OP_ENCODE / _DECODE /
+// _ENCODE_SYS / _DECODE_SYS): plan-level matrices now, per-pattern buffers
+// reserved for later.  Synchronises the device.
+int direct_enable(fnt_rs_plan_s* p, int op) {
   if (!direct_available(p)) return FNT_RS_E_ARG;
-  const uint32_t n = p->n, k = p->k;
-  DirectState* s = new DirectState();
-  p->direct = s;
-  const char* e = std::getenv("FNTRS_DIRECT_SIMT");
-  s->simt = e && e[0] == '1';
-  auto fail = [&](int rc) {
-    direct_free(p);
-    return rc;
-  };
-  const uint32_t r = hp(3, 65536u / n);
-  std::vector<uint32_t> xs(k), pts(n - k), G;
-  for (uint32_t i = 0; i < k; ++i) xs[i] = hp(r, i);
-  for (uint32_t j = k; j < n; ++j) pts[j - k] = hp(r, j);
-  lagrange_rows(xs, pts, G);
-  std::vector<uint32_t> gc = centring(G, k);
-  int rc;
-  // G | gcorr, and D | mrow | cmap | dcorr
-  const size_t gwords = std::max<size_t>(1, G.size() + gc.size());
-  const size_t dwords = (size_t)k * k + k + 2 * (size_t)k + k;
-  if ((rc = cuda_ok(cudaMalloc(&s->G, gwords * 4)))) return fail(rc);
-  s->gcorr = s->G + G.size();
-  if ((rc = cuda_ok(cudaMalloc(&s->D, dwords * 4)))) return fail(rc);
-  s->mrow = s->D + (size_t)k * k;
-  s->cmap = reinterpret_cast<uint2*>(s->mrow + k);
-  s->dcorr = s->mrow + 3 * (size_t)k;
-  if (!G.empty() &&
-      ((rc = cuda_ok(cudaMemcpy(s->G, G.data(), G.size() * 4, cudaMemcpyHostToDevice))) ||
-       (rc = cuda_ok(cudaMemcpy(s->gcorr, gc.data(), gc.size() * 4, cudaMemcpyHostToDevice)))))
-    return fail(rc);
-  if (!s->simt) {
-    if ((rc = cuda_ok(cudaMalloc(&s->Gl, std::max<size_t>(16, limb_bytes((int)(n - k), (int)k))))))
-      return fail(rc);
-    if ((rc = cuda_ok(cudaMalloc(&s->Dl, limb_bytes((int)k, (int)k))))) return fail(rc);
-    if ((rc = limbs_a(p, s->G, (int)(n - k), (int)k, s->Gl, nullptr))) return fail(rc);
-    if ((rc = cuda_ok(cudaDeviceSynchronize()))) return fail(rc);
+  if (!p->direct) {
+    p->direct = new DirectState();
+    const char* e = std::getenv("FNTRS_DIRECT_SIMT");
+    p->direct->simt = e && e[0] == '1';
   }
-  return FNT_RS_OK;
+  DirectState* s = p->direct;
+  const uint32_t n = p->n, k = p->k;
+  const uint32_t r = root_of(n);
+  int rc = FNT_RS_OK;
+  if (op == FNT_RS_OP_ENCODE_SYS && !s->G.a) {
+    std::vector<uint32_t> xs(k), pts(n - k), G;
+    for (uint32_t i = 0; i < k; ++i) xs[i] = hp(r, i);
+    for (uint32_t j = k; j < n; ++j) pts[j - k] = hp(r, j);
+    lagrange_rows(xs, pts, G);
+    if ((rc = mat_alloc(s->G, (int)(n - k), (int)k, s->simt)) ||
+        (rc = mat_upload(p, s->G, G, (int)(n - k), (int)k, s->simt, nullptr)))
+      return rc;
+  } else if (op == FNT_RS_OP_ENCODE && !s->V.a) {
+    std::vector<uint32_t> V((size_t)n * k);
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t rj = hp(r, j);
+      uint32_t x = 1;
+      for (uint32_t i = 0; i < k; ++i, x = hm(x, rj)) V[(size_t)j * k + i] = x;
+    }
+    if ((rc = mat_alloc(s->V, (int)n, (int)k, false)) ||
+        (rc = mat_upload(p, s->V, V, (int)n, (int)k, false, nullptr)))
+      return rc;
+  } else if (op == FNT_RS_OP_DECODE_SYS && !s->D.a) {
+    if ((rc = mat_alloc(s->D, (int)k, (int)k, s->simt))) return rc;
+    const size_t k2 = (k + 1) & ~1u;  // cmap (8-byte entries) starts 8-byte aligned
+    if (!s->mrow && (rc = cuda_ok(cudaMalloc(&s->mrow, k2 * 4 + (size_t)k * 8)))) return rc;
+    s->cmap = reinterpret_cast<uint2*>(s->mrow + k2);
+  } else if (op == FNT_RS_OP_DECODE && !s->Mi.a) {
+    if ((rc = mat_alloc(s->Mi, (int)k, (int)k, false))) return rc;
+    if ((rc = cuda_ok(cudaMalloc(&s->rmap, (size_t)k * 4)))) return rc;
+  }
+  return cuda_ok(cudaDeviceSynchronize());
+}
+
+bool direct_ready(const fnt_rs_plan_s* p, int op) {
+  const DirectState* s = p->direct;
+  if (!s) return false;
+  switch (op) {
+    case FNT_RS_OP_ENCODE_SYS: return s->G.a != nullptr;
+    case FNT_RS_OP_ENCODE: return s->V.a != nullptr;
+    case FNT_RS_OP_DECODE_SYS: return s->D.a != nullptr;
+    case FNT_RS_OP_DECODE: return s->Mi.a != nullptr;
+    default: return false;
+  }
 }
 
 int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                       size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
   DirectState* s = p->direct;
-  if (!s) return FNT_RS_E_ARG;
+  if (!direct_ready(p, FNT_RS_OP_ENCODE_SYS)) return FNT_RS_E_ARG;
   if (!s->simt && !workspace) return FNT_RS_E_WORKSPACE;
   const int k = (int)p->k;
   const int M = (int)(p->n_out - p->k);
   if (!s->simt)  // the systematic rows are copied by the kernel that splits the source
-    return gemm_tc<uint16_t>(p, s->Gl, s->gcorr, M, src, ld_src, (int)W, workspace, enc,
+    return gemm_tc<uint16_t>(p, s->G.limbs, s->G.corr, M, src, ld_src, (int)W, workspace, enc,
                              (size_t)k, nullptr, nullptr, ld_enc, st, enc, ld_enc);
   k_copy_src<<<grid_for(p, (size_t)k * W), 256, 0, st>>>(src, ld_src, enc, ld_enc, k, (int)W);
   count_launch();
   const int rc = cuda_ok(cudaGetLastError());
   if (rc) return rc;
-  return launch_gemm<uint16_t>(s->G, M, k, src, ld_src, (int)W, enc, (size_t)k, nullptr, nullptr,
-                               ld_enc, p->status, st);
+  return launch_gemm<uint16_t>(s->G.a, M, k, src, ld_src, (int)W, enc, (size_t)k, nullptr,
+                               nullptr, ld_enc, p->status, st);
 }
 
 int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
                       const uint32_t* positions, uint16_t* out, size_t ld_out, size_t W,
                       void* workspace, cudaStream_t st) {
   DirectState* s = p->direct;
-  if (!s) return FNT_RS_E_ARG;
+  if (!direct_ready(p, FNT_RS_OP_DECODE_SYS)) return FNT_RS_E_ARG;
   if (!s->simt && !workspace) return FNT_RS_E_WORKSPACE;
   const uint32_t n = p->n, k = p->k;
   std::vector<uint32_t> key(positions, positions + k);
-  if (!s->pattern_ready || s->key != key) {
-    s->pattern_ready = false;
-    const uint32_t r = hp(3, 65536u / n);
+  if (!s->d_ready || s->dkey != key) {
+    s->d_ready = false;
+    const uint32_t r = root_of(n);
     std::vector<uint32_t> xs(k), pts, mrow, D;
     std::vector<uint2> cmap;
     std::vector<char> got(k, 0);
@@ -626,25 +709,18 @@ int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
         mrow.push_back(m);
       }
     lagrange_rows(xs, pts, D);
-    std::vector<uint32_t> dc = centring(D, k);
-    int rc;
-    // pageable sources: each copy has staged its data when it returns
-    if (!D.empty() && ((rc = cuda_ok(cudaMemcpyAsync(s->D, D.data(), D.size() * 4,
-                                                     cudaMemcpyHostToDevice, st))) ||
-                       (rc = cuda_ok(cudaMemcpyAsync(s->dcorr, dc.data(), dc.size() * 4,
-                                                     cudaMemcpyHostToDevice, st))) ||
-                       (rc = cuda_ok(cudaMemcpyAsync(s->mrow, mrow.data(), mrow.size() * 4,
-                                                     cudaMemcpyHostToDevice, st)))))
-      return rc;
-    if (!cmap.empty() && (rc = cuda_ok(cudaMemcpyAsync(s->cmap, cmap.data(), cmap.size() * 8,
-                                                       cudaMemcpyHostToDevice, st))))
-      return rc;
-    if (!s->simt && !D.empty() && (rc = limbs_a(p, s->D, (int)mrow.size(), (int)k, s->Dl, st)))
-      return rc;
+    int rc = mat_upload(p, s->D, D, (int)mrow.size(), (int)k, s->simt, st);
+    if (!rc && !mrow.empty())
+      rc = cuda_ok(cudaMemcpyAsync(s->mrow, mrow.data(), mrow.size() * 4, cudaMemcpyHostToDevice,
+                                   st));
+    if (!rc && !cmap.empty())
+      rc = cuda_ok(cudaMemcpyAsync(s->cmap, cmap.data(), cmap.size() * 8, cudaMemcpyHostToDevice,
+                                   st));
+    if (rc) return rc;
     s->nmiss = (int)mrow.size();
     s->ncopy = (int)cmap.size();
-    s->key.swap(key);
-    s->pattern_ready = true;
+    s->dkey.swap(key);
+    s->d_ready = true;
   }
   if (s->ncopy) {
     k_copy_recv<<<grid_for(p, (size_t)s->ncopy * W), 256, 0, st>>>(recv, ld_recv, s->cmap,
@@ -654,11 +730,69 @@ int direct_decode_sys(fnt_rs_plan_s* p, const uint32_t* recv, size_t ld_recv,
     const int rc = cuda_ok(cudaGetLastError());
     if (rc) return rc;
   }
-  if (s->simt)
-    return launch_gemm<uint32_t>(s->D, s->nmiss, (int)k, recv, ld_recv, (int)W, nullptr, 0, out,
-                                 s->mrow, ld_out, p->status, st);
-  return gemm_tc<uint32_t>(p, s->Dl, s->dcorr, s->nmiss, recv, ld_recv, (int)W, workspace,
-                           nullptr, 0, out, s->mrow, ld_out, st);
+  return product<uint32_t>(p, s->D, recv, ld_recv, (int)W, workspace, nullptr, 0, out, s->mrow,
+                           ld_out, st, s->simt);
+}
+
+int direct_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                  size_t ld_enc, size_t W, void* workspace, cudaStream_t st) {
+  DirectState* s = p->direct;
+  if (!direct_ready(p, FNT_RS_OP_ENCODE)) return FNT_RS_E_ARG;
+  if (!workspace) return FNT_RS_E_WORKSPACE;
+  DirectMat v = s->V;
+  v.rows = (int)p->n_out;  // a punctured code keeps the first n_out rows
+  return product<uint16_t>(p, v, src, ld_src, (int)W, workspace, enc, 0, nullptr, nullptr,
+                           ld_enc, st, false);
+}
+
+int direct_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, size_t ld_recv,
+                  uint16_t* out, size_t ld_out, size_t W, void* workspace, cudaStream_t st,
+                  int slots, uint32_t* out32) {
+  DirectState* s = p->direct;
+  if (!direct_ready(p, FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
+  if (!workspace) return FNT_RS_E_WORKSPACE;
+  const uint32_t n = p->n, k = p->k;
+  std::vector<uint32_t> key = sl.key;
+  if (&sl == &p->sys) {
+    key.resize(k);
+    for (uint32_t i = 0; i < k; ++i) key[i] = i;
+  }
+  if (!s->m_ready || s->mkey != key) {
+    s->m_ready = false;
+    // M[i][l] = coefficient i of L_l(x) = w_l A(x) / (x - x_l), A = prod (x - x_m)
+    const uint32_t r = root_of(n);
+    std::vector<uint32_t> xs(k), A(k + 1, 0), M((size_t)k * k), q(k), wl(k), dA(k);
+    for (uint32_t l = 0; l < k; ++l) xs[l] = hp(r, key[l]);
+    A[0] = 1;
+    for (uint32_t m = 0; m < k; ++m) {  // multiply by (x - x_m)
+      for (uint32_t i = m + 1; i > 0; --i) A[i] = (A[i - 1] + hm(kPh - xs[m], A[i])) % kPh;
+      A[0] = hm(kPh - xs[m], A[0]);
+    }
+    std::vector<std::vector<uint32_t>> Q(k);
+    for (uint32_t l = 0; l < k; ++l) {
+      // synthetic division: Q = A / (x - x_l), degree k-1; A'(x_l) = Q(x_l)
+      q[k - 1] = A[k];
+      for (uint32_t i = k - 1; i > 0; --i) q[i - 1] = (A[i] + hm(xs[l], q[i])) % kPh;
+      uint32_t v = 0;
+      for (uint32_t i = k; i-- > 0;) v = (hm(v, xs[l]) + q[i]) % kPh;
+      dA[l] = v;
+      Q[l] = q;
+    }
+    batch_inverse(dA, wl);
+    for (uint32_t l = 0; l < k; ++l)
+      for (uint32_t i = 0; i < k; ++i) M[(size_t)i * k + l] = hm(wl[l], Q[l][i]);
+    int rc = mat_upload(p, s->Mi, M, (int)k, (int)k, false, st);
+    if (!rc) rc = cuda_ok(cudaMemcpyAsync(s->rmap, key.data(), (size_t)k * 4,
+                                          cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    s->mkey.swap(key);
+    s->m_ready = true;
+  }
+  // tensor cores only: the source limbs are split off before the product, so the
+  // output may overwrite the received rows (the systematic code's in-place use)
+  return product<uint32_t>(p, s->Mi, recv, ld_recv, (int)W, workspace, out32, 0,
+                           out32 ? nullptr : out, nullptr, ld_out, st, false,
+                           slots ? s->rmap : nullptr);
 }
 
 }  // namespace fntrs

@@ -187,8 +187,14 @@ int paper_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, 
 
 // The direct (quadratic) systematic encoder and decoder (direct.cu).
 bool direct_available(const fnt_rs_plan_s* p);
-int direct_enable(fnt_rs_plan_s* p);
+int direct_enable(fnt_rs_plan_s* p, int op);  // op: FNT_RS_OP_ENCODE / _DECODE / _ENCODE_SYS / _DECODE_SYS
+bool direct_ready(const fnt_rs_plan_s* p, int op);
 void direct_free(fnt_rs_plan_s* p);
+int direct_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
+                  size_t ld_enc, size_t W, void* workspace, cudaStream_t st);
+int direct_decode(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv, size_t ld_recv,
+                  uint16_t* out, size_t ld_out, size_t W, void* workspace, cudaStream_t st,
+                  int slots, uint32_t* out32);
 size_t direct_ws_bytes(const fnt_rs_plan_s* p, size_t W);
 int direct_encode_sys(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                       size_t ld_enc, size_t W, void* workspace, cudaStream_t st);

@@ -268,6 +268,7 @@ bool sched_available(const fnt_rs_plan_s* p, int op, int s) {
       case FNT_RS_SCHED_TMA: return p->enc_L != 0 && p->u == 1 && !p->no_tma;
       case FNT_RS_SCHED_TILE: return n <= (uint32_t)kTileMaxL;
       case FNT_RS_SCHED_SPLIT: return n > 8192;
+      case FNT_RS_SCHED_DIRECT: return direct_available(p);
       default: return false;
     }
   }
@@ -279,6 +280,7 @@ bool sched_available(const fnt_rs_plan_s* p, int op, int s) {
       case FNT_RS_SCHED_TILE: return !p->split;
       case FNT_RS_SCHED_SPLIT: return n >= 16384;
       case FNT_RS_SCHED_PAPER: return paper_available(p);
+      case FNT_RS_SCHED_DIRECT: return direct_available(p);
       default: return false;
     }
   }
@@ -307,11 +309,13 @@ int dec_nbuf_max(const fnt_rs_plan_s* p) { return p->n >= 16384 ? (p->blocked ? 
 int fnt_nbuf(const fnt_rs_plan_s* p) { return p->split ? 1 : 0; }
 
 size_t dec_ws_now(const fnt_rs_plan_s* p, size_t W) {
-  if (sched_effective(p, FNT_RS_OP_DECODE) == FNT_RS_SCHED_PAPER) return paper_ws_bytes(p, W);
+  const int s = sched_effective(p, FNT_RS_OP_DECODE);
+  if (s == FNT_RS_SCHED_PAPER) return paper_ws_bytes(p, W);
+  if (s == FNT_RS_SCHED_DIRECT) return direct_ws_bytes(p, W);
   return ws_bytes(p, W, dec_nbuf(p));
 }
 size_t dec_ws_max(const fnt_rs_plan_s* p, size_t W) {
-  return std::max(ws_bytes(p, W, dec_nbuf_max(p)), paper_ws_bytes(p, W));
+  return std::max({ws_bytes(p, W, dec_nbuf_max(p)), paper_ws_bytes(p, W), direct_ws_bytes(p, W)});
 }
 
 static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
@@ -667,7 +671,14 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
 int do_encode(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint32_t* enc,
                      size_t ld_enc, size_t W, void* workspace, cudaStream_t st,
                      const WireSpec* wire) {
-  const int sched = sched_effective(p, FNT_RS_OP_ENCODE);
+  int sched = sched_effective(p, FNT_RS_OP_ENCODE);
+  if (sched == FNT_RS_SCHED_DIRECT) {
+    if (!wire) return direct_encode(p, src, ld_src, enc, ld_enc, W, workspace, st);
+    // the 16-bit wire output is written by the transform kernels only
+    sched = sched_available(p, FNT_RS_OP_ENCODE, FNT_RS_SCHED_TMA)
+                ? FNT_RS_SCHED_TMA
+                : (p->n <= 8192 ? FNT_RS_SCHED_TILE : FNT_RS_SCHED_SPLIT);
+  }
   if (sched == FNT_RS_SCHED_TMA) {
     const int t = encode_tma(p, src, ld_src, enc, ld_enc, W, st, wire);
     if (t != 1) return t;  // else (unaligned pointers) the one-CTA tile below
@@ -813,6 +824,8 @@ int do_decode_tables(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* re
   const int sched = sched_effective(p, FNT_RS_OP_DECODE);
   if (sched == FNT_RS_SCHED_PAPER)
     return paper_decode(p, sl, recv, ld_recv, out, ld_out, W, workspace, st, slots, out32);
+  if (sched == FNT_RS_SCHED_DIRECT)
+    return direct_decode(p, sl, recv, ld_recv, out, ld_out, W, workspace, st, slots, out32);
   if (!slots && sched == FNT_RS_SCHED_TMA) {
     const int t = decode_tma(p, sl, recv, ld_recv, out, ld_out, W, st, out32);
     if (t != 1) return t;  // else (unaligned rows) the one-CTA tile below
@@ -1080,8 +1093,9 @@ size_t fnt_rs_workspace_bytes(fnt_rs_plan p, size_t W, int op) {
   if (!p) return 0;
   switch (op) {
     case FNT_RS_OP_ENCODE:
-      return ws_bytes(p, W, enc_nbuf_max(p)) +
-             (p->n_out < p->n ? align256((size_t)p->n * W * 4) : 0);
+      return std::max(ws_bytes(p, W, enc_nbuf_max(p)) +
+                          (p->n_out < p->n ? align256((size_t)p->n * W * 4) : 0),
+                      direct_ws_bytes(p, W));
     case FNT_RS_OP_ENCODE_SYS:
     case FNT_RS_OP_DECODE_SYS: return sys_workspace_bytes(p, W);
     case FNT_RS_OP_DECODE: return dec_ws_max(p, W);
@@ -1103,6 +1117,11 @@ int fnt_rs_encode(fnt_rs_plan p, const uint16_t* src, size_t ld_src, uint32_t* e
   if (!p || W == 0) return W == 0 && p ? FNT_RS_OK : FNT_RS_E_ARG;
   if (!src || !enc || ld_src < W || ld_enc < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(src, 2) || !aligned(enc, 4)) return FNT_RS_E_ARG;
+  if (sched_effective(p, FNT_RS_OP_ENCODE) == FNT_RS_SCHED_DIRECT) {
+    // the direct product writes the n_out rows of a punctured code itself
+    if (direct_ws_bytes(p, W) && !workspace) return FNT_RS_E_WORKSPACE;
+    return direct_encode(p, src, ld_src, enc, ld_enc, W, workspace, S(stream));
+  }
   if (p->n_out == p->n) {
     if (ws_bytes(p, W, enc_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
     return do_encode(p, src, ld_src, enc, ld_enc, W, workspace, S(stream));
@@ -1249,7 +1268,7 @@ int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
     if (sched != FNT_RS_SCHED_AUTO && sched != FNT_RS_SCHED_DIRECT) return FNT_RS_E_ARG;
     if (sched == FNT_RS_SCHED_DIRECT) {
       if (!direct_available(p)) return FNT_RS_E_ARG;
-      const int rc = direct_enable(p);
+      const int rc = direct_enable(p, op);
       if (rc) return rc;
     }
     (op == FNT_RS_OP_ENCODE_SYS ? p->sched_sys_enc : p->sched_sys_dec) = sched;
@@ -1259,6 +1278,10 @@ int fnt_rs_set_schedule(fnt_rs_plan p, int op, int sched) {
   if (sched != FNT_RS_SCHED_AUTO && !sched_available(p, op, sched)) return FNT_RS_E_ARG;
   if (sched == FNT_RS_SCHED_PAPER) {
     const int rc = paper_enable(p, nullptr);
+    if (rc) return rc;
+  }
+  if (sched == FNT_RS_SCHED_DIRECT) {
+    const int rc = direct_enable(p, op);
     if (rc) return rc;
   }
   (op == FNT_RS_OP_ENCODE ? p->sched_enc : p->sched_dec) = sched;
@@ -1279,15 +1302,21 @@ int fnt_rs_autotune(fnt_rs_plan p, size_t W, int op, fnt_rs_tune_result* out, in
                     void* stream) {
   if (!p || W == 0 || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
   std::vector<int> cand;
-  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_CPA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT})
+  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_CPA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT,
+                FNT_RS_SCHED_DIRECT})
     if (sched_available(p, op, s)) cand.push_back(s);
   if (cand.empty()) return FNT_RS_E_ARG;
+  // the direct product's matrices (and tensor-core tiles) are built before timing
+  if (std::find(cand.begin(), cand.end(), FNT_RS_SCHED_DIRECT) != cand.end() &&
+      direct_enable(p, op) != FNT_RS_OK)
+    cand.erase(std::find(cand.begin(), cand.end(), FNT_RS_SCHED_DIRECT));
   cudaStream_t st = S(stream);
   const size_t n = p->n, k = p->k;
   size_t w = std::min(W, std::max<size_t>(8, ((size_t)1 << 29) / (n * 4)));
   if (w >= 8) w = w / 8 * 8;
   const bool enc_op = op == FNT_RS_OP_ENCODE;
-  const size_t wsb = ws_bytes(p, w, enc_op ? enc_nbuf_max(p) : dec_nbuf_max(p));
+  const size_t wsb = std::max(ws_bytes(p, w, enc_op ? enc_nbuf_max(p) : dec_nbuf_max(p)),
+                              direct_ws_bytes(p, w));
   uint16_t* src = nullptr;
   uint32_t* enc = nullptr;
   uint16_t* dout = nullptr;

@@ -94,7 +94,9 @@ def test_direct_availability_and_switch_back(pkg):
     with pytest.raises(pkg.FntRsError):
         plan.set_schedule(pkg.OP_ENCODE_SYS, pkg.SCHED_DIRECT)
     with pytest.raises(pkg.FntRsError):
-        pkg.Plan(256, 100).set_schedule(pkg.OP_ENCODE, pkg.SCHED_DIRECT)
+        plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_DIRECT)  # the non-systematic ones too
+    with pytest.raises(pkg.FntRsError):
+        pkg.Plan(256, 100).set_schedule(pkg.OP_FNT, pkg.SCHED_DIRECT)  # not an op with schedules
     plan = _direct_plan(pkg, 256, 100)
     plan.set_schedule(pkg.OP_ENCODE_SYS, pkg.SCHED_AUTO)
     assert plan.schedule(pkg.OP_ENCODE_SYS) != pkg.SCHED_DIRECT
@@ -120,3 +122,67 @@ def test_tensor_core_and_integer_products_agree(pkg, monkeypatch):
         got = pkg.to_host(plan.decode_sys(pkg.to_device(v), pos))
         assert np.array_equal(got, want_d), simt
         plan.status()
+
+
+def _direct_code_plan(pkg, n, k):
+    plan = pkg.Plan(n, k)
+    plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_DIRECT)
+    plan.set_schedule(pkg.OP_DECODE, pkg.SCHED_DIRECT)
+    assert plan.schedule(pkg.OP_DECODE) == pkg.SCHED_DIRECT
+    return plan
+
+
+@pytest.mark.parametrize("n,k,W", [(2, 1, 3), (16, 5, 9), (64, 20, 70), (512, 256, 130),
+                                   (2048, 1024, 40), (16384, 256, 8)])
+def test_direct_nonsystematic_code_matches_oracle(pkg, n, k, W):
+    """Encode e = V s with V[j][i] = r^(ij) and decode s = M v with M the Lagrange-basis
+    coefficients of the received points, as tensor-core products (Sec. II.A's matrix view
+    of the code, Sec. III's quadratic methods)."""
+    seed = 7 * n + k
+    src = synth.source(seed, k, W)
+    plan = _direct_code_plan(pkg, n, k)
+    enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+    if n <= 2048:
+        assert np.array_equal(enc, oracle.encode(src, n))
+    else:
+        rows = np.array([0, 1, n // 2, n - 1], np.uint32)
+        assert np.array_equal(enc[rows], oracle.encode_rows(src, n, rows))
+    pos = synth.received_positions(n, synth.erased_uniform(seed + 1, n, k))
+    assert np.array_equal(pkg.to_host(plan.decode(pkg.to_device(np.ascontiguousarray(enc[pos])),
+                                                  pos)), src)
+    assert plan.status() == 0
+    v = synth.received_uniform(seed + 2, k, W)
+    got = pkg.to_host(plan.decode(pkg.to_device(v), pos))
+    want, flag = oracle.decode(v, pos, n, k)
+    assert np.array_equal(got, want)
+    assert (plan.status() == pkg.E_RANGE) == flag
+
+
+def test_direct_code_slots_systematic_punctured_and_tuner(pkg):
+    n, k, W = 1024, 300, 72
+    src = synth.source(91, k, W)
+    plan = _direct_code_plan(pkg, n, k)
+    enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+    pos = synth.received_positions(n, synth.erased_burst(92, n, k))
+    # slot buffer: row z = position z
+    assert np.array_equal(pkg.to_host(plan.decode_slots(pkg.to_device(enc), pos)), src)
+    # the systematic FNT route interpolates through the decode schedule (u32 coefficients)
+    es = pkg.to_host(plan.encode_sys(pkg.to_device(src)))
+    assert np.array_equal(es, oracle.encode_sys(src, n))
+    # punctured: the direct product writes the first n_out rows
+    plan.set_length(700)
+    e2 = pkg.to_host(plan.encode(pkg.to_device(src)))
+    assert e2.shape[0] == 700 and np.array_equal(e2, enc[:700])
+    plan.set_length(n)
+    assert plan.status() == 0
+    # the tuner times the direct product beside the transform schedules
+    t = pkg.Plan(512, 128)
+    for op in (pkg.OP_ENCODE, pkg.OP_DECODE):
+        res = t.autotune(256, op)
+        assert pkg.SCHED_DIRECT in [r[0] for r in res]
+    src2 = synth.source(93, 128, 256)
+    e3 = pkg.to_host(t.encode(pkg.to_device(src2)))
+    assert np.array_equal(e3, oracle.encode(src2, 512))
+    pos2 = synth.received_positions(512, synth.erased_uniform(94, 512, 128))
+    assert np.array_equal(pkg.to_host(t.decode(pkg.to_device(np.ascontiguousarray(e3[pos2])),
+                                               pos2)), src2)
