@@ -420,6 +420,11 @@ int fnt_rs_status(fnt_rs_plan plan, void* stream);
  * `nstreams` streams, their plans' schedules picked by fnt_rs_autotune on the
  * widest group of each plan (environment FNTRS_AUTOTUNE=0 keeps the default
  * schedules).  Groups must not share output buffers.
+ * Failure-detection test hook: with the environment variable
+ * FNTRS_TEST_STALL_GROUP=g at creation, the decode items of persistent group
+ * g wait for one encode tile more than the group has (a stalled producer);
+ * their bounded waits give up, FNT_RS_E_TIMEOUT is raised in the status word
+ * and that group's decode is skipped, everything else completes.
  */
 typedef struct fnt_rs_group_s {
   uint32_t n, k;

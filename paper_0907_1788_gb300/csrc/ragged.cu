@@ -96,6 +96,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   d.blocked = p->blocked ? 1 : 0;
   d.has_plan = g.positions ? 1 : 0;
   d.enc_tiles = (int)((g.W + ragged_wt_enc(n) - 1) / ragged_wt_enc(n));
+  d.enc_need = d.enc_tiles;
   KArgs& e = d.enc;
   e.in = g.src;
   e.ld_in = g.ld_src;
@@ -270,8 +271,16 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     std::stable_sort(pers.begin(), pers.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::vector<RaggedGroupDev> dg;
     std::vector<RaggedItem> items;
+    // Failure-detection test hook: FNTRS_TEST_STALL_GROUP=g makes the decode
+    // items of group g wait for one encode tile more than the group has (a
+    // producer that never finishes).  Their bounded waits give up, raise
+    // FNT_RS_E_TIMEOUT in the group's status and skip its decode; every other
+    // item runs as usual and the launch ends.
+    const char* stall_env = std::getenv("FNTRS_TEST_STALL_GROUP");
+    const int stall = stall_env ? std::atoi(stall_env) : -1;
     for (int gi = 0; gi < (int)pers.size(); ++gi) {
       dg.push_back(make_dev_group(r->groups[pers[gi]]));
+      if (pers[gi] == stall) dg.back().enc_need += 1;
       for (int t = 0; t < dg.back().enc_tiles; ++t) items.push_back({RI_ENC, gi, t});
     }
     for (int gi = 0; gi < (int)pers.size(); ++gi)

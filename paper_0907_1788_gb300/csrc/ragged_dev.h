@@ -28,6 +28,7 @@ struct RaggedGroupDev {
   int L;          // n
   int blocked;    // k > n/2: two-buffer decode, tables from the coefficient split
   int enc_tiles;  // encode tiles this group contributes (its decode waits for all of them)
+  int enc_need;   // encode tiles a decode item waits for (= enc_tiles; see FNTRS_TEST_STALL_GROUP)
   int has_plan;   // decode group
 };
 

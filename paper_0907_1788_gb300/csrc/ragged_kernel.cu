@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
       }
     } else {
       if (threadIdx.x == 0) {
-        const bool ok = wait_at_least(ra.enc_done + item.group, (unsigned)g.enc_tiles) &&
+        const bool ok = wait_at_least(ra.enc_done + item.group, (unsigned)g.enc_need) &&
                         (!g.has_plan || wait_at_least(ra.plan_done + item.group, 1u));
         if (!ok) atomicOr(g.dec.status, ST_TIMEOUT);
         __threadfence();
