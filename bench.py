@@ -346,6 +346,58 @@ def systematic_measure(pkg, dev, reps=20):
                       "(pattern cached) and with positions 0..k-1 received; L2 flushed"}
 
 
+def large_code_measure(pkg, dev, reps=5):
+    """The maximum length k = 32768, n = 65536 with 1024 codewords (2 KB packets), burst and
+    uniform erasures: encode, pattern build and decode times (the split transforms)."""
+    import torch
+
+    res = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for name in ("k32768_n65536_w1024_burst", "k32768_n65536_w1024_uniform"):
+        cfg = synth.CONFIGS[name]
+        n, k, W = cfg.n, cfg.k, cfg.W
+        plan = pkg.Plan(n, k, device=dev)
+        src = cfg.source()
+        d_src = pkg.to_device(src, dev)
+        enc = torch.empty((n, W), dtype=torch.int32, device=dev)
+        out = torch.empty((k, W), dtype=torch.int16, device=dev)
+        ws_e = plan.workspace(W, pkg.OP_ENCODE)
+        ws_d = plan.workspace(W, pkg.OP_DECODE)
+        pos = cfg.positions()
+        pkg.fnt_rs_encode(plan.handle, d_src, enc, ws_e)
+        recv = torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
+        rng = np.random.default_rng(cfg.seed)
+
+        def timed(fn):
+            fn()
+            ts = []
+            for i in range(reps):
+                flush.fill_(i & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+
+        te = timed(lambda: pkg.fnt_rs_encode(plan.handle, d_src, enc, ws_e))
+        # a fresh pattern each time: the first k positions of a new permutation
+        tp = timed(lambda: plan.prepare(rng.permutation(n)[:k].astype(np.uint32)))
+        plan.prepare(pos)
+        td = timed(lambda: pkg.fnt_rs_decode(plan.handle, recv, pos, out, ws_d))
+        ok = np.array_equal(pkg.to_host(out), src) and plan.status() == 0
+        gb = k * W * 2 / 1e9
+        res[name] = {"encode_ms": te, "plan_ms": tp, "decode_ms": td,
+                     "encode_gbs": gb / (te * 1e-3), "decode_gbs": gb / (td * 1e-3),
+                     "decode_incl_plan_gbs": gb / ((td + tp) * 1e-3), "round_trip_ok": bool(ok),
+                     "schedules": {"encode": pkg.SCHED_NAMES[plan.schedule(pkg.OP_ENCODE)],
+                                   "decode": pkg.SCHED_NAMES[plan.schedule(pkg.OP_DECODE)]}}
+        plan.close()
+    res["config"] = "L2 flushed between calls; the plan time includes the host-side pattern upload"
+    return res
+
+
 def direct_measure(pkg, dev, n=512, k=256, W=2048, reps=20):
     """The systematic code on a short code (k = 256, n = 512, 4 KB packets): the FNT
     route against the paper's direct (quadratic) encoder and decoder."""
@@ -815,6 +867,7 @@ def run_gpu(args):
         line["wire"] = wire_measure(pkg, dev)
         line["paper_route"] = paper_route_measure(pkg, dev)
         line["direct"] = direct_measure(pkg, dev)
+        line["large"] = large_code_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
