@@ -122,8 +122,9 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *   FNT_RS_SCHED_SPLIT  radix-(n/4096) cross passes and 4096-point local
  *                       passes through the workspace (encode n > 8192,
  *                       decode n >= 16384),
- *   FNT_RS_SCHED_CPA    decode only: half-width tiles staged by cp.async,
- *                       two CTAs per SM (n = 4096 or 8192, k <= n/2),
+ *   FNT_RS_SCHED_CPA    decode only: tiles staged by cp.async (k <= n/2):
+ *                       half-width tiles, two CTAs per SM, for n = 4096 or
+ *                       8192; two-codeword tiles for n = 16384,
  *   FNT_RS_SCHED_PAPER  decode only: the paper's own route (Sec. II.B/III):
  *                       step 3 by the chirp (per pattern), step 5 as a
  *                       middle product and step 6 as a product, both by
@@ -143,9 +144,9 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *                       device); the workspace covers it once selected.  A
  *                       16-bit wire encode (fnt_rs_encode_wire) keeps the
  *                       transform schedules.
- * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else TILE
- * (encode up to n = 8192; decode wherever one CTA holds the codeword), else
- * SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
+ * FNT_RS_SCHED_AUTO (the default) takes TMA where it applies, else (decode
+ * of n = 16384, k <= n/2) CPA, else TILE (encode up to n = 8192; decode
+ * wherever one CTA holds the codeword), else SPLIT.  fnt_rs_workspace_bytes covers every schedule of the plan.
  */
 enum fnt_rs_sched {
   FNT_RS_SCHED_AUTO = 0,

@@ -91,9 +91,9 @@ void launch_plan_fused(const PlanArgs& pa, cudaStream_t st) {
   count_launch();
 }
 
-template <class S, int WT, int NT, bool HALF>
+template <class S, int WT, int NT, bool HALF, int MINB>
 int launch_decode_cpa_h(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
-  auto kern = k_decode_cpa<S, WT, NT, HALF>;
+  auto kern = k_decode_cpa<S, WT, NT, HALF, MINB>;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
   auto bytes = [&](int k) { return work + ((k * WT + 3) / 4 * 4) * 4 + kSchedBytes; };
   static bool done[64] = {};
@@ -110,10 +110,10 @@ int launch_decode_cpa_h(const KArgs& a, const uint32_t* pat32, cudaStream_t st) 
   return 0;
 }
 
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, int MINB = 2>
 int launch_decode_cpa_t(const KArgs& a, const uint32_t* pat32, cudaStream_t st) {
-  if (2 * a.k == S::L) return launch_decode_cpa_h<S, WT, NT, true>(a, pat32, st);
-  return launch_decode_cpa_h<S, WT, NT, false>(a, pat32, st);
+  if (2 * a.k == S::L) return launch_decode_cpa_h<S, WT, NT, true, MINB>(a, pat32, st);
+  return launch_decode_cpa_h<S, WT, NT, false, MINB>(a, pat32, st);
 }
 
 template <int L>
@@ -141,6 +141,11 @@ TileOps make_tile_ops() {
   if constexpr (L == 4096 || L == 8192) {
     ops.decode_cpa = &launch_decode_cpa_t<S, W1 / 2, 256>;
     ops.wt_cpa = W1 / 2;
+  } else if constexpr (L == 16384) {
+    // two codewords per CTA as in the one-CTA tile, rows staged by 8-byte
+    // copies (a TMA row would need 16 bytes); one CTA per SM
+    ops.decode_cpa = &launch_decode_cpa_t<S, 2, 512, 1>;
+    ops.wt_cpa = 2;
   }
   return ops;
 }

@@ -838,8 +838,8 @@ __global__ void __launch_bounds__(NT, 1)
 // 16-byte (WT = 4) aligned.
 // smem: work (Lay WORDS u32) | stage (k * WT u32) | barriers and cancel response.
 // ---------------------------------------------------------------------------
-template <class S, int WT, int NT, bool HALF>
-__global__ void __launch_bounds__(NT, 2)
+template <class S, int WT, int NT, bool HALF, int MINB = 2>
+__global__ void __launch_bounds__(NT, MINB)
     k_decode_cpa(KArgs a, const uint32_t* __restrict__ pat32) {
   static_assert(S::NP >= 2 && (WT == 2 || WT == 4), "");
   using Y = Lay<S, WT>;
