@@ -124,7 +124,8 @@ int fnt_rs_encode(fnt_rs_plan plan, const uint16_t* src, size_t ld_src, uint32_t
  *                       decode n >= 16384),
  *   FNT_RS_SCHED_CPA    decode only: tiles staged by cp.async (k <= n/2):
  *                       half-width tiles, two CTAs per SM, for n = 4096 or
- *                       8192; two-codeword tiles for n = 16384,
+ *                       8192; the one-CTA tile's two (one) codewords for
+ *                       n = 16384 (32768),
  *   FNT_RS_SCHED_PAPER  decode only: the paper's own route (Sec. II.B/III):
  *                       step 3 by the chirp (per pattern), step 5 as a
  *                       middle product and step 6 as a product, both by

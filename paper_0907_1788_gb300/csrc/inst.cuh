@@ -141,11 +141,11 @@ TileOps make_tile_ops() {
   if constexpr (L == 4096 || L == 8192) {
     ops.decode_cpa = &launch_decode_cpa_t<S, W1 / 2, 256>;
     ops.wt_cpa = W1 / 2;
-  } else if constexpr (L == 16384) {
-    // two codewords per CTA as in the one-CTA tile, rows staged by 8-byte
+  } else if constexpr (L == 16384 || L == 32768) {
+    // the one-CTA tile's two (one) codewords, rows staged by 8-byte (4-byte)
     // copies (a TMA row would need 16 bytes); one CTA per SM
-    ops.decode_cpa = &launch_decode_cpa_t<S, 2, 512, 1>;
-    ops.wt_cpa = 2;
+    ops.decode_cpa = &launch_decode_cpa_t<S, W1, 512, 1>;
+    ops.wt_cpa = W1;
   }
   return ops;
 }

@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(NT, 1)
 template <class S, int WT, int NT, bool HALF, int MINB = 2>
 __global__ void __launch_bounds__(NT, MINB)
     k_decode_cpa(KArgs a, const uint32_t* __restrict__ pat32) {
-  static_assert(S::NP >= 2 && (WT == 2 || WT == 4), "");
+  static_assert(S::NP >= 2 && (WT == 1 || WT == 2 || WT == 4), "");
   using Y = Lay<S, WT>;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
   extern __shared__ __align__(128) uint4 smem_raw[];

@@ -749,7 +749,7 @@ int do_encode_two_pass(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uin
 static int decode_cpa(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* recv,
                       size_t ld_recv, uint16_t* out, size_t ld_out, size_t W, cudaStream_t st,
                       uint32_t* out32) {
-  if (p->split || p->blocked || p->n > 16384) return 1;
+  if (p->split || p->blocked || p->n > 32768) return 1;
   const TileOps& ops = tile_ops((int)p->n);
   if (!ops.decode_cpa) return 1;
   const size_t row_bytes = (size_t)ops.wt_cpa * 4;  // 8 or 16: the copy size

@@ -61,11 +61,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Asynchronous global -> shared copy of BYTES (8 or 16) bytes of which the
+// Asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes of which the
 // first `valid` are read and the rest zero-filled (cp.async, LDGSTS).
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* dst, const void* src, int valid) {
-  static_assert(BYTES == 8 || BYTES == 16, "");
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "");
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src),
                "n"(BYTES), "r"(valid)
                : "memory");

@@ -123,8 +123,8 @@ def test_every_schedule_gives_the_same_words(pkg, n, k, W):
     plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_AUTO)
     plan.set_schedule(pkg.OP_DECODE, pkg.SCHED_AUTO)
     assert len(encs) >= 1 and len(decs) >= 1
-    if n > 8192:  # one-CTA tile and split both run (and the staged tile at 16384, k <= n/2)
-        assert len(encs) == 2 and len(decs) == (3 if (n == 16384 and 2 * k <= n) else 2)
+    if n > 8192:  # one-CTA tile and split both run (and the staged tile for k <= n/2)
+        assert len(encs) == 2 and len(decs) == (3 if (n in (16384, 32768) and 2 * k <= n) else 2)
     first_e, first_d = next(iter(encs.values())), next(iter(decs.values()))
     for e in encs.values():
         assert np.array_equal(e, first_e)
