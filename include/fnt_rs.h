@@ -26,6 +26,10 @@
  * (NULL = legacy default stream).  Calls enqueue work and return without
  * synchronising, except where noted.
  *
+ * Empty batches: W = 0 is a valid batch of no codewords; its data pointers
+ * may be NULL and nothing is launched (a decode still validates the
+ * positions and builds or finds their pattern).
+ *
  * Errors: every int-returning call returns FNT_RS_OK (0) or a negative
  * FNT_RS_E_* code; no exception crosses the ABI.  Argument errors are
  * detected on the host before any launch.  Data-dependent conditions found

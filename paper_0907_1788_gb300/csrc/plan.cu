@@ -1148,7 +1148,7 @@ int fnt_rs_decode(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv, const uin
                   uint32_t npos, uint16_t* out, size_t ld_out, size_t W, void* workspace,
                   void* stream) {
   if (!p) return FNT_RS_E_ARG;
-  if (!recv || !out || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if ((W && (!recv || !out)) || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(recv, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
   if (dec_ws_now(p, W) && !workspace) return FNT_RS_E_WORKSPACE;
   int rc = prepare(p, positions, npos, S(stream));
@@ -1162,7 +1162,7 @@ int fnt_rs_decode_slots(fnt_rs_plan p, const uint32_t* slots, size_t ld_slots,
                         const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
                         size_t W, void* workspace, void* stream) {
   if (!p) return FNT_RS_E_ARG;
-  if (!slots || !out || ld_slots < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if ((W && (!slots || !out)) || ld_slots < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(slots, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
   if (dec_ws_now(p, W) && !workspace) return FNT_RS_E_WORKSPACE;
   if (p->u != 1) return FNT_RS_E_ROOT;  // slot rows follow the default root's positions
@@ -1177,7 +1177,7 @@ int fnt_rs_decode_full(fnt_rs_plan p, const uint32_t* enc, size_t ld_enc, uint16
                        size_t ld_out, size_t W, void* workspace, void* stream) {
   if (!p || p->n_out < p->n) return FNT_RS_E_ARG;  // a punctured codeword is never complete
   if (W == 0) return FNT_RS_OK;
-  if (!enc || !out || ld_enc < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if ((W && (!enc || !out)) || ld_enc < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned(enc, 4) || !aligned(out, 2)) return FNT_RS_E_ARG;
   if (ws_bytes(p, W, fnt_nbuf(p)) && !workspace) return FNT_RS_E_WORKSPACE;
   cudaStream_t st = S(stream);

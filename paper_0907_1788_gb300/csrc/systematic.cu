@@ -142,7 +142,7 @@ int fnt_rs_decode_sys(fnt_rs_plan p, const uint32_t* recv, size_t ld_recv,
                       const uint32_t* positions, uint32_t npos, uint16_t* out, size_t ld_out,
                       size_t W, void* workspace, void* stream) {
   if (!p) return FNT_RS_E_ARG;
-  if (!recv || !out || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if ((W && (!recv || !out)) || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned_to(recv, 4) || !aligned_to(out, 2)) return FNT_RS_E_ARG;
   if (p->u != 1) return FNT_RS_E_ROOT;
   int rc = validate_positions(p, positions, npos);

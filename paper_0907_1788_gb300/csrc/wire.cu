@@ -145,7 +145,7 @@ int fnt_rs_decode_wire(fnt_rs_plan p, const uint16_t* recv, size_t ld_recv,
                        uint32_t nesc, uint16_t* out, size_t ld_out, size_t W, void* workspace,
                        void* stream) {
   if (!p) return FNT_RS_E_ARG;
-  if (!recv || !out || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
+  if ((W && (!recv || !out)) || ld_recv < W || ld_out < W || W > (1u << 30)) return FNT_RS_E_ARG;
   if (!aligned_to(recv, 2) || !aligned_to(out, 2) || (nesc && !esc) || !aligned_to(esc, 8))
     return FNT_RS_E_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
