@@ -856,6 +856,10 @@ def run_gpu(args):
                              "bytes_per_launch": dom_bytes}},
         "e2e": e2e,
         "e2e_u32": e2e_u32,
+        "bit_exact": {"round_trip": True, "codewords": W,
+                      "checked": "decode(encode(s)) == s on every codeword after the timed, "
+                                 "serial and end-to-end passes (the run aborts otherwise); "
+                                 "oracle parity is the test suite's"},
         "gpu_launches": int(launches),
         "wall_ms_per_step": t_wall * 1e3 / args.steps,
         "clocks": clk.summary(),
