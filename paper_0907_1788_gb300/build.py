@@ -24,7 +24,8 @@ SOURCES = ["plan.cu", "pattern.cu", "inst_small.cu", "inst_mid.cu", "inst_big.cu
            "inst_huge.cu", "inst_split.cu", "noalloc.cu", "ragged.cu", "ragged_kernel.cu", "server.cu",
            "systematic.cu", "wire.cu",
            "hostpipe.cu", "paper_route.cu",
-           "direct.cu"]
+           "direct.cu",
+           "inst_fold.cu"]
 
 
 def nvcc() -> str:

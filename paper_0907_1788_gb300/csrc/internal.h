@@ -80,6 +80,7 @@ struct fnt_rs_plan_s {
   uint32_t* ghat = nullptr;  // [n][D] transforms of the reversed digit vectors
   uint32_t* exp3 = nullptr;  // shared table
   int enc_L = 0, enc_C = 0;  // TMA encode shape (0: not applicable)
+  bool enc_fold = false;     // n = 8192, k > 4096: the classes fold two source rows
   bool no_tma = false;
   int sched_enc = 0, sched_dec = 0;  // fnt_rs_sched of encode / decode (0: automatic)
   int sms = 1;

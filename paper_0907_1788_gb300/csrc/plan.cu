@@ -55,6 +55,8 @@ const TileOps& tile_ops(int L) {
 int launch_encode_tma_small(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 int launch_encode_tma_mid(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 int launch_encode_tma_big(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
+// n = 8192 with k > 4096: the two classes fold two source rows (inst_fold.cu)
+int launch_encode_tma_fold(const KArgs& a, const TmaEncodeArgs& t, cudaStream_t st);
 
 int launch_decode_tma_small(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
 int launch_decode_tma_mid(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);
@@ -635,8 +637,9 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   if ((reinterpret_cast<uintptr_t>(src) % 16) != 0 || (ld_src * 2) % 16 != 0) return 1;
   auto fn = tmap_encode_fn();
   if (!fn) return 1;
+  if (p->enc_fold && wire) return 1;  // the folding kernel writes u32 symbols only
   const int L = p->enc_L, C = p->enc_C;
-  const int WT = tile_ops(L).wt1;
+  const int WT = tile_ops(L).wt1;  // 8 codewords of 16-bit source: one 16-byte TMA row
   const int box_rows = std::min(256, L);
   const int rows_staged = (int)((p->k + box_rows - 1) / box_rows) * box_rows;
   CUtensorMap map;
@@ -666,7 +669,8 @@ static int encode_tma(fnt_rs_plan_s* p, const uint16_t* src, size_t ld_src, uint
   t.box_rows = box_rows;
   t.grid = ntiles;  // one CTA per tile; running CTAs take over pending ones
   t.map = &map;
-  if (launch_encode_tma(L, C, a, t, st) != 0) return 1;
+  if ((p->enc_fold ? launch_encode_tma_fold(a, t, st) : launch_encode_tma(L, C, a, t, st)) != 0)
+    return 1;
   return cuda_ok(cudaGetLastError());
 }
 
@@ -1006,9 +1010,10 @@ int fnt_rs_plan_create(fnt_rs_plan* out, uint32_t n, uint32_t k, uint32_t p_, ui
     if (n >= 64 && n <= 4096) {
       p->enc_L = (int)n;
       p->enc_C = 1;
-    } else if (n == 8192 && k <= 4096) {
+    } else if (n == 8192) {
       p->enc_L = 4096;
       p->enc_C = 2;
+      p->enc_fold = k > 4096;
     }
     if (p->enc_L && (rc = get_tables(p->enc_L, &p->tenc))) return fail(rc);
     const char* pe = std::getenv("FNTRS_PLAN");

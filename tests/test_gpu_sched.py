@@ -150,3 +150,28 @@ def test_autotune_keeps_the_fastest_schedule(pkg):
         enc = pkg.to_host(plan.encode(pkg.to_device(src)))
         assert np.array_equal(pkg.to_host(plan.decode(pkg.to_device(enc[pos]), pos)), src)
         assert plan.status() == 0
+
+
+@pytest.mark.parametrize("k,W", [(4097, 40), (6144, 16), (7000, 9), (8191, 24), (8192, 8)])
+def test_high_rate_n8192_encode_folds_on_tma(pkg, k, W):
+    """n = 8192, k > 4096: the TMA encode folds rows i and i + 4096 into its two
+    output classes; it must give the oracle's words and the generic tile's."""
+    n = 8192
+    src = synth.source(k + W, k, W)
+    plan = pkg.Plan(n, k)
+    assert plan.schedule(pkg.OP_ENCODE) == pkg.SCHED_TMA  # the default for these codes now
+    enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+    cols = sorted({0, W // 2, W - 1})
+    rows = np.sort(np.random.default_rng(k).choice(n, 64, replace=False)).astype(np.uint32)
+    want = oracle.encode_rows(np.ascontiguousarray(src[:, cols]), n, rows)
+    assert np.array_equal(enc[rows][:, cols], want)
+    plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_TILE)
+    assert np.array_equal(pkg.to_host(plan.encode(pkg.to_device(src))), enc)
+    plan.set_schedule(pkg.OP_ENCODE, pkg.SCHED_AUTO)
+    # the 16-bit wire output keeps the generic tile for these codes
+    sym, _ = plan.encode_wire(pkg.to_device(src))
+    assert np.array_equal(pkg.to_host(sym), (enc & 0xFFFF).astype(np.uint16))
+    pos = synth.received_positions(n, synth.erased_uniform(k, n, k))
+    out = pkg.to_host(plan.decode(pkg.to_device(np.ascontiguousarray(enc[pos])), pos))
+    assert np.array_equal(out, src)
+    assert plan.status() == 0
