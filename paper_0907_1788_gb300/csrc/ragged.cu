@@ -359,8 +359,9 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     if (rg.persistent) continue;
     rg.stream = assign[rg.plan];
     fnt_rs_plan_s* p = rg.plan;
-    size_t need = ws_bytes(p, rg.g.W, enc_nbuf_max(p));
-    if (rg.g.positions) need = std::max(need, ws_bytes(p, rg.g.W, dec_nbuf_max(p)));
+    // every schedule the plan may run (the tuner may have picked the direct product)
+    size_t need = std::max(ws_bytes(p, rg.g.W, enc_nbuf_max(p)), direct_ws_bytes(p, rg.g.W));
+    if (rg.g.positions) need = std::max(need, dec_ws_max(p, rg.g.W));
     wsb[rg.stream] = std::max(wsb[rg.stream], need);
   }
   for (uint32_t s = 0; s < S; ++s) {
