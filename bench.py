@@ -117,7 +117,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(),
+                                 f"fntrs_clocks_rank{index}_{os.getpid()}.csv")
 
     def _lines(self):
         try:
