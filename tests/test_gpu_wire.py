@@ -281,3 +281,27 @@ def test_host_calls_in_chunks(pkg, W):
                                 h_out, plan.workspace(W, pkg.OP_DECODE_WIRE_HOST))
     assert np.array_equal(h_out.numpy().view(np.uint16), src)
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("n,k,W", [(512, 200, 24), (16384, 5000, 4)])
+def test_wire_with_a_custom_root(pkg, n, k, W):
+    """Another root of order n defines another MDS code (rows permuted by the
+    index map); the wire output must follow it, escapes at the permuted rows."""
+    r = oracle.root(n)
+    root = pow(r, 7, P)
+    src = synth.source(n + 3, k, W)
+    plan = pkg.Plan(n, k, root=root)
+    sym, esc = plan.encode_wire(pkg.to_device(src))
+    sym, esc = pkg.to_host(sym), pkg.to_host(esc).reshape(-1, 2)
+    rows = np.sort(np.random.default_rng(n).choice(n, 40, replace=False)).astype(np.uint32)
+    want = oracle.encode_rows(src, n, rows, root_=root)
+    assert np.array_equal(sym[rows], (want & 0xFFFF).astype(np.uint16))
+    for j, c in esc.tolist():
+        assert oracle.encode_rows(np.ascontiguousarray(src[:, [c]]), n, np.array([j], np.uint32),
+                                  root_=root)[0, 0] == 65536
+    pos = synth.received_positions(n, synth.erased_uniform(n + 4, n, k))
+    resc = wire.select_rows(esc, pos)
+    out = plan.decode_wire(pkg.to_device(np.ascontiguousarray(sym[pos])), pos,
+                           pkg.to_device(resc) if len(resc) else None)
+    assert np.array_equal(pkg.to_host(out), src)
+    assert plan.status() == 0
