@@ -546,12 +546,14 @@ int gemm_tc(fnt_rs_plan_s* p, const uint16_t* Al, const uint32_t* corr, int M, c
             size_t ld_copy = 0, const uint32_t* rmap = nullptr) {
   if (W <= 0 || (M <= 0 && !copy)) return FNT_RS_OK;
   if (reinterpret_cast<uintptr_t>(work) % 16 != 0) return FNT_RS_E_ARG;  // bulk-copy source
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[64] = {};  // the opt-in is per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!attr[dev & 63]) {
     if (cudaFuncSetAttribute(k_fp_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kTcSmem) != cudaSuccess)
       return FNT_RS_E_CUDA;
-    attr = true;
+    attr[dev & 63] = true;
   }
   const int K = (int)p->k, Kc = kchunks(K);
   uint16_t* Bl = static_cast<uint16_t*>(work);
