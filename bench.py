@@ -349,6 +349,54 @@ def systematic_measure(pkg, dev, reps=20):
                       "(pattern cached) and with positions 0..k-1 received; L2 flushed"}
 
 
+def rate_measure(pkg, dev, n=8192, W=2048, reps=10):
+    """Encode and decode at n = 8192 for the code rates of the ragged and serving
+    workloads (k/n = 1/2, 2/3, 3/4, 7/8), pattern cached, L2 flushed."""
+    import torch
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {}
+    for num, den in ((1, 2), (2, 3), (3, 4), (7, 8)):
+        k = n * num // den
+        plan = pkg.Plan(n, k, device=dev)
+        src = synth.source(k, k, W)
+        d_src = pkg.to_device(src, dev)
+        enc = torch.empty((n, W), dtype=torch.int32, device=dev)
+        out = torch.empty((k, W), dtype=torch.int16, device=dev)
+        ws_e = plan.workspace(W, pkg.OP_ENCODE)
+        ws_d = plan.workspace(W, pkg.OP_DECODE)
+        pos = synth.received_positions(n, synth.erased_uniform(k + 1, n, k))
+        pkg.fnt_rs_encode(plan.handle, d_src, enc, ws_e)
+        recv = torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
+        plan.prepare(pos)
+        te = timed(lambda: pkg.fnt_rs_encode(plan.handle, d_src, enc, ws_e))
+        td = timed(lambda: pkg.fnt_rs_decode(plan.handle, recv, pos, out, ws_d))
+        ok = np.array_equal(pkg.to_host(out), src) and plan.status() == 0
+        gb = k * W * 2 / 1e9
+        res[f"{num}/{den}"] = {
+            "k": k, "encode_ms": te, "decode_ms": td, "encode_gbs": gb / (te * 1e-3),
+            "decode_gbs": gb / (td * 1e-3), "round_trip_ok": bool(ok),
+            "schedules": {"encode": pkg.SCHED_NAMES[plan.schedule(pkg.OP_ENCODE)],
+                          "decode": pkg.SCHED_NAMES[plan.schedule(pkg.OP_DECODE)]}}
+        plan.close()
+    res["config"] = f"n={n}, W={W}, uniform erasures, pattern cached, L2 flushed"
+    return res
+
+
 def large_code_measure(pkg, dev, reps=5):
     """The maximum length k = 32768, n = 65536 with 1024 codewords (2 KB packets), burst and
     uniform erasures: encode, pattern build and decode times (the split transforms)."""
@@ -878,6 +926,7 @@ def run_gpu(args):
         line["paper_route"] = paper_route_measure(pkg, dev)
         line["direct"] = direct_measure(pkg, dev)
         line["large"] = large_code_measure(pkg, dev)
+        line["rates"] = rate_measure(pkg, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
