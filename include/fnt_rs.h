@@ -185,9 +185,11 @@ int fnt_rs_set_schedule(fnt_rs_plan plan, int op, int sched);
 int fnt_rs_get_schedule(fnt_rs_plan plan, int op);
 
 /*
- * Autotuner.  Runs every schedule of `op` that can run this plan (but
- * FNT_RS_SCHED_PAPER; FNT_RS_SCHED_DIRECT included, whose matrices it builds
- * and keeps in the plan) on W codewords of zeroed data (at most 2^29 bytes of encoded words: a larger W
+ * Autotuner.  Runs every transform schedule of `op` that can run this plan
+ * (TMA, CPA, TILE, SPLIT: never FNT_RS_SCHED_PAPER or FNT_RS_SCHED_DIRECT, so
+ * a tuned plan computes its encode and decode on the integer pipes only; the
+ * tensor-core product runs only when selected by fnt_rs_set_schedule) on W
+ * codewords of zeroed data (at most 2^29 bytes of encoded words: a larger W
  * is timed on fewer columns, a multiple of 8) in device buffers it allocates
  * and frees itself, times each with CUDA events on `stream` (median of 5
  * calls after 2 warm-up calls; the time of an integer transform does not
@@ -280,7 +282,8 @@ int fnt_rs_decode_host(fnt_rs_plan plan, const uint32_t* h_recv, const uint32_t*
 /*
  * Encode without any allocation, scratch included (the paper has no
  * counterpart; this is a deployment convenience).  Codes with n > 8192 are
- * encoded in two passes that exchange data through n * W words of scratch;
+ * encoded in two passes that exchange data through n * W words of scratch, and
+ * a punctured code is encoded at full length into n * W words first;
  * fnt_rs_encode takes that scratch from the caller, this call takes it from a
  * fixed device array of FNT_RS_NOALLOC_SCRATCH_BYTES that the library keeps on
  * every GPU it is loaded on until the process exits.  It is meant for callers
@@ -290,9 +293,13 @@ int fnt_rs_decode_host(fnt_rs_plan plan, const uint32_t* h_recv, const uint32_t*
  * pipelines that must not hit cudaMalloc's implicit device synchronisation or
  * an out-of-memory failure in the middle of a stream.
  *   - Same arguments and result as fnt_rs_encode, minus the workspace.
- *   - n * W * 4 > FNT_RS_NOALLOC_SCRATCH_BYTES: returns FNT_RS_E_WORKSPACE
- *     without launching anything (split the batch into smaller W).
- *   - n <= 8192 needs no scratch and simply runs fnt_rs_encode.
+ *   - fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_ENCODE) above
+ *     FNT_RS_NOALLOC_SCRATCH_BYTES: returns FNT_RS_E_WORKSPACE without
+ *     launching anything (split the batch into smaller W).  For an unpunctured
+ *     code that size is n * W * 4 (capped by the column chunking); a punctured
+ *     code with n > 8192 needs about twice that.
+ *   - A code that needs no scratch (n <= 8192, not punctured) simply runs
+ *     fnt_rs_encode.
  *   - The first call on a device looks up the array's device address; make
  *     that first call before any stream capture.
  *   - All calls share the one array: calls that overlap on the GPU race.

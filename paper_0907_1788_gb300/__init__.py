@@ -151,8 +151,10 @@ def fnt_rs_encode_noalloc(plan, src: torch.Tensor, enc: torch.Tensor, stream=Non
 
     For callers that cannot allocate device memory while running (all memory
     reserved up front, or no cudaMalloc allowed on the hot path).  Requests
-    with n * W * 4 bytes above FNT_RS_NOALLOC_SCRATCH_BYTES raise FntRsError
-    (code -9); concurrent calls on different streams share the scratch.
+    whose encode workspace (fnt_rs_workspace_bytes: n * W * 4 for a long
+    code, about twice that for a punctured one) is above
+    FNT_RS_NOALLOC_SCRATCH_BYTES raise FntRsError (code -9) before anything
+    is launched; concurrent calls on different streams share the scratch.
     """
     W, ld_src = _cols(src)
     W2, ld_enc = _cols(enc)

@@ -1,8 +1,9 @@
 // Encode for long codes (n > 8192) that allocates nothing at call time.
 //
 // Codes longer than one CTA's tile are encoded in two passes that meet in a
-// scratch matrix of n * W words.  fnt_rs_encode takes that scratch from the
-// caller; fnt_rs_encode_noalloc takes it from the fixed device array below,
+// scratch matrix of n * W words, and a punctured code is first encoded at full
+// length into a buffer of n * W words.  fnt_rs_encode takes that scratch from
+// the caller; fnt_rs_encode_noalloc takes it from the fixed device array below,
 // which every GPU that loads this library keeps until the process exits.
 // Calls share the array: two calls that overlap on the GPU (different
 // streams, or graphs replayed concurrently) race on it.  Nothing in it has to
@@ -49,14 +50,12 @@ extern "C" int fnt_rs_encode_noalloc(fnt_rs_plan plan, const uint16_t* src, size
                                      uint32_t* enc, size_t ld_enc, size_t W, void* stream) {
   using namespace fntrs;
   if (!plan) return FNT_RS_E_ARG;
+  // everything the regular call may use from its workspace: the split scratch
+  // and, for a punctured code, the full-length codeword buffer in front of it
   const size_t need = fnt_rs_workspace_bytes(plan, W, FNT_RS_OP_ENCODE);
   if (need == 0)  // short codes use no scratch: the regular entry point allocates nothing
     return fnt_rs_encode(plan, src, ld_src, enc, ld_enc, W, nullptr, stream);
-  // the regular path works in column chunks; the whole request must fit at once here
-  int info[8] = {0};
-  fnt_rs_plan_info(plan, info, 8);
-  const size_t n = (size_t)info[0];
-  if (n * W * 4 > FNT_RS_NOALLOC_SCRATCH_BYTES) return FNT_RS_E_WORKSPACE;
+  if (need > FNT_RS_NOALLOC_SCRATCH_BYTES) return FNT_RS_E_WORKSPACE;
   void* scratch = nullptr;
   const int rc = noalloc_scratch(&scratch);
   if (rc) return rc;

@@ -948,8 +948,8 @@ const char* fnt_rs_strerror(int code) {
     case FNT_RS_E_RANGE: return "value out of range (decoded 65536 or received > 65536)";
     case FNT_RS_E_TIMEOUT: return "a bounded device wait gave up";
     case FNT_RS_E_WORKSPACE:
-      return "workspace missing or too small (or, for fnt_rs_encode_noalloc, n * W * 4 "
-             "exceeds FNT_RS_NOALLOC_SCRATCH_BYTES)";
+      return "workspace missing or too small (or, for fnt_rs_encode_noalloc, the encode "
+             "workspace exceeds FNT_RS_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown status";
   }
 }
@@ -1309,15 +1309,13 @@ int fnt_rs_get_schedule(fnt_rs_plan p, int op) {
 int fnt_rs_autotune(fnt_rs_plan p, size_t W, int op, fnt_rs_tune_result* out, int cap,
                     void* stream) {
   if (!p || W == 0 || (op != FNT_RS_OP_ENCODE && op != FNT_RS_OP_DECODE)) return FNT_RS_E_ARG;
+  // Only the transform schedules (integer pipes) are candidates: the plain code's
+  // encode and decode never switch to the tensor-core product by themselves;
+  // FNT_RS_SCHED_DIRECT stays an explicit choice through fnt_rs_set_schedule.
   std::vector<int> cand;
-  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_CPA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT,
-                FNT_RS_SCHED_DIRECT})
+  for (int s : {FNT_RS_SCHED_TMA, FNT_RS_SCHED_CPA, FNT_RS_SCHED_TILE, FNT_RS_SCHED_SPLIT})
     if (sched_available(p, op, s)) cand.push_back(s);
   if (cand.empty()) return FNT_RS_E_ARG;
-  // the direct product's matrices (and tensor-core tiles) are built before timing
-  if (std::find(cand.begin(), cand.end(), FNT_RS_SCHED_DIRECT) != cand.end() &&
-      direct_enable(p, op) != FNT_RS_OK)
-    cand.erase(std::find(cand.begin(), cand.end(), FNT_RS_SCHED_DIRECT));
   cudaStream_t st = S(stream);
   const size_t n = p->n, k = p->k;
   size_t w = std::min(W, std::max<size_t>(8, ((size_t)1 << 29) / (n * 4)));

@@ -54,3 +54,41 @@ def test_noalloc_short_code_and_size_limit(pkg):
     with pytest.raises(pkg.FntRsError) as ei:
         pkg.fnt_rs_encode_noalloc(big.handle, src, out)
     assert ei.value.code == -9
+
+
+def test_noalloc_punctured_long_code_refused_beyond_scratch(pkg):
+    # A punctured code is encoded at full length into a buffer of n * W words,
+    # with the long code's two-pass scratch behind it: about twice n * W * 4
+    # bytes.  Here n * W * 4 is just above 8 MiB, so the whole workspace is
+    # above the 16 MiB array and the call must be refused before any launch.
+    n, k, n_out = 16384, 8192, 12000
+    plan = pkg.Plan(n, k)
+    plan.set_length(n_out)
+    W = (8 << 20) // (n * 4) + 8
+    need = pkg.fnt_rs_workspace_bytes(plan.handle, W, pkg.OP_ENCODE)
+    assert n * W * 4 <= pkg.NOALLOC_SCRATCH_BYTES < need
+    src = pkg.to_device(synth.source(11, k, W))
+    out = torch.full((n_out, W), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    before = pkg.fnt_rs_launch_count()
+    with pytest.raises(pkg.FntRsError) as ei:
+        pkg.fnt_rs_encode_noalloc(plan.handle, src, out)
+    assert ei.value.code == -9
+    assert pkg.fnt_rs_launch_count() == before
+    torch.cuda.synchronize()
+    assert bool((out == -1).all())
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("n,k,n_out,W", [(16384, 8192, 12000, 64), (8192, 4096, 6000, 200)])
+def test_noalloc_punctured_within_limit_matches_regular(pkg, n, k, n_out, W):
+    plan = pkg.Plan(n, k)
+    plan.set_length(n_out)
+    assert 0 < pkg.fnt_rs_workspace_bytes(plan.handle, W, pkg.OP_ENCODE) <= pkg.NOALLOC_SCRATCH_BYTES
+    for call in range(2):
+        src = pkg.to_device(synth.source(77 + call, k, W))
+        want = plan.encode(src)  # caller workspace
+        got = torch.full((n_out, W), -1, dtype=torch.int32, device="cuda")
+        pkg.fnt_rs_encode_noalloc(plan.handle, src, got)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
