@@ -33,6 +33,7 @@ WORKLOAD = synth.CONFIGS["k4096_n8192_w2048"]
 METRIC = "RS encode/decode source GB/s on 1 GB300 (% HBM roof, bit-exact); serving p50/p99 ms"
 UNIT = "GB/s"
 N_PATTERNS = 8  # more than the plan's 4 cached patterns: every step rebuilds
+N_SETS = 3  # source / encoded / decoded buffer sets the timed steps rotate over
 
 
 def _peaks():
@@ -265,8 +266,12 @@ def ragged_measure(pkg, dev, budget_bytes=6 << 30, nstreams=16):
                        "that fit one 6 GB wave; each group = encode + pattern build + decode")}
 
 
-def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30, patterns_per_shape=64):
-    """cfg5 trace head: continuous batching server vs one request at a time."""
+def serving_measure(pkg, rate=5000.0, count=3000, budget=32 << 30, patterns_per_shape=64):
+    """cfg5 trace head: continuous batching server vs one request at a time.
+
+    Both arms count each request's latency from its scheduled arrival
+    (replay start + arrival time) to the moment its result is seen, so
+    queueing and any late submission are included on the same clock."""
     reqs = synth.serving_requests(seed=5, rate_per_s=rate, duration_s=count / rate * 2,
                                   patterns_per_shape=patterns_per_shape)[:count]
     trace = []
@@ -298,6 +303,7 @@ def serving_measure(pkg, rate=5000.0, count=300, budget=32 << 30, patterns_per_s
                          "achieved_gbs": src / bwall / 1e9, "wall_s": bwall,
                          "kind": "one request at a time, plan + pattern built per request"},
             "budget_gb": budget / 2**30, "streams": 16,
+            "latency_clock": "scheduled arrival -> result seen, both arms",
             "config": ("seed-5 Poisson trace (n = 2^U{9..16}, rho in {1/2,3/4}, packets "
                        f"2^U{{10..14}} B, half decode with {patterns_per_shape} recurring patterns "
                        f"per shape), first {len(trace)} requests; inputs generated on the device")}
@@ -624,7 +630,7 @@ def paper_route_measure(pkg, dev, reps=10):
     return res
 
 
-def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=300):
+def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=3000):
     """The cfg5 arrival rates, each on the head of its seeded trace, plus a
     fresh-pattern variant (every decode request brings a new erasure pattern)."""
     runs = [serving_measure(pkg, rate=r, count=count) for r in rates]
@@ -727,6 +733,14 @@ def run_gpu(args):
     pkg.fnt_rs_encode(plan.handle, src, enc, plan.workspace(W, pkg.OP_ENCODE), stream)
     recvs = [torch.index_select(enc, 0, torch.from_numpy(pos.astype(np.int64)).to(dev))
              for pos in patterns]
+    # Steady state: source, encoded and decoded buffers rotate over N_SETS copies
+    # (with the 8 received matrices: 544 MB touched per rotation, > the 129 MB L2),
+    # so nothing a step reads is left in L2 by the step before, and the dirty
+    # lines a step leaves are written back during the steps after it, inside
+    # their events.
+    srcs = [src] + [src.clone() for _ in range(N_SETS - 1)]
+    encs = [enc] + [torch.empty_like(enc) for _ in range(N_SETS - 1)]
+    outs = [out] + [torch.empty_like(out) for _ in range(N_SETS - 1)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ws_e = plan.workspace(W, pkg.OP_ENCODE)
     ws_d = plan.workspace(W, pkg.OP_DECODE)
@@ -741,37 +755,43 @@ def run_gpu(args):
 
     def step(i, ev=None):
         pos = patterns[i % N_PATTERNS]
+        b = i % N_SETS
         if ev:
             ev[0].record(stream)
         fork.record(stream)
         pkg.fnt_rs_decode_prepare(plan.handle, pos, stream)
         side.wait_event(fork)
-        pkg.fnt_rs_encode(plan.handle, src, enc, ws_e, side)
+        pkg.fnt_rs_encode(plan.handle, srcs[b], encs[b], ws_e, side)
         join.record(side)
-        pkg.fnt_rs_decode(plan.handle, recvs[i % N_PATTERNS], pos, out, ws_d, stream)
+        pkg.fnt_rs_decode(plan.handle, recvs[i % N_PATTERNS], pos, outs[b], ws_d, stream)
         stream.wait_event(join)
         if ev:
             ev[1].record(stream)
 
+    def round_trip_ok():
+        want = cfg.source()
+        return all(np.array_equal(pkg.to_host(o), want) for o in outs)
+
     def step_serial(i, ev):
         # the same work one call after another, to time each phase on its own
         pos = patterns[i % N_PATTERNS]
+        b = i % N_SETS
         ev[0].record(stream)
-        pkg.fnt_rs_encode(plan.handle, src, enc, ws_e, stream)
+        pkg.fnt_rs_encode(plan.handle, srcs[b], encs[b], ws_e, stream)
         ev[1].record(stream)
         pkg.fnt_rs_decode_prepare(plan.handle, pos, stream)
         ev[2].record(stream)
-        pkg.fnt_rs_decode(plan.handle, recvs[i % N_PATTERNS], pos, out, ws_d, stream)
+        pkg.fnt_rs_decode(plan.handle, recvs[i % N_PATTERNS], pos, outs[b], ws_d, stream)
         ev[3].record(stream)
 
-    for i in range(args.warmup):
-        flush.fill_(i & 0xFF)
+    for i in range(max(args.warmup, N_SETS)):
         step(i)
     torch.cuda.synchronize()
     # correctness of the timed configuration (bit-exact round trip)
-    assert np.array_equal(pkg.to_host(out), cfg.source()), "round trip failed"
+    assert round_trip_ok(), "round trip failed"
     assert plan.status() == 0
 
+    # timed region: steps back to back, no flush (buffers rotate, see above)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     launches0 = pkg.fnt_rs_launch_count()
     if world > 1:
@@ -780,7 +800,6 @@ def run_gpu(args):
     with Clocks(local) as clk:
         t_wall0 = time.perf_counter()
         for i in range(args.steps):
-            flush.fill_((i + 7) & 0xFF)
             step(args.warmup + i, evs[i])
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
@@ -789,8 +808,20 @@ def run_gpu(args):
     launches = pkg.fnt_rs_launch_count() - launches0
     ms_step = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     ms_step = max_over_ranks(ms_step, dev)
-    assert np.array_equal(pkg.to_host(out), cfg.source()), "round trip failed (timed)"
+    assert round_trip_ok(), "round trip failed (timed)"
     assert plan.status() == 0
+
+    # the same steps with L2 flushed before each (the flush outside the events):
+    # cold reads, and the write-back of a step's output left outside its events
+    fev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_((i + 7) & 0xFF)
+        step(args.warmup + i, fev[i])
+    torch.cuda.synchronize()
+    ms_flushed = sum(e[0].elapsed_time(e[1]) for e in fev) / args.steps
+    ms_flushed = max_over_ranks(ms_flushed, dev)
+    assert round_trip_ok(), "round trip failed (flushed)"
 
     # per-phase times (and the dominant kernel's duration for the roofline) from
     # the same steps run serially
@@ -804,7 +835,7 @@ def run_gpu(args):
     t_pat = [e[1].elapsed_time(e[2]) for e in sev]
     t_dec = [e[2].elapsed_time(e[3]) for e in sev]
     ms_serial = (sum(t_enc) + sum(t_pat) + sum(t_dec)) / args.steps
-    assert np.array_equal(pkg.to_host(out), cfg.source()), "round trip failed (serial)"
+    assert round_trip_ok(), "round trip failed (serial)"
 
     src_bytes = k * W * 2
     value = whole_job_gbs(src_bytes, world, ms_step)
@@ -824,6 +855,16 @@ def run_gpu(args):
         dom_kernel = "k_encode_tma"
     achieved_tops = dom_instr / (dom_ms * 1e-3) / 1e12
     achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9
+
+    def kernel_roof(ms, nbytes, ninstr):
+        tops = ninstr / (ms * 1e-3) / 1e12
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"us": ms * 1e3, "issue_frac": tops / ISSUE_PEAK_TOPS,
+                "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "bytes_per_launch": nbytes,
+                "modelled_instr_per_launch": ninstr}
+
+    per_kernel = {"k_decode_tma": kernel_roof(dec_ms, dec_bytes, W * decode_instr(n, k)),
+                  "k_encode_tma": kernel_roof(enc_ms, enc_bytes, W * encode_instr(n, k))}
 
     # end to end through the host-buffer entry points (pinned memory)
     h_src = torch.from_numpy(cfg.source().view(np.int16)).pin_memory()
@@ -892,11 +933,18 @@ def run_gpu(args):
         "config": {"workload": cfg.name, "n": n, "k": k, "W": W, "packet_bytes": 2 * W,
                    "erasures": "uniform, fresh pattern per step (8 cycling > 4 cached)",
                    "step": "(decode plan -> decode of k received packets) || encode, two streams",
-                   "l2": "flushed between steps (256 MB write, outside the events)",
+                   "l2": (f"not flushed: inputs larger than L2 (source, encoded and decoded "
+                          f"buffers rotate over {N_SETS} sets, 8 received matrices; 544 MB "
+                          "touched per rotation > 129 MB L2); each step's write-back lands "
+                          "inside later steps' events"),
                    "parallelism": f"replicas x{world}"},
         "autotune": tuned,
         "breakdown_ms": {"encode": enc_ms, "plan": pat_ms, "decode": dec_ms,
                          "serial_step": ms_serial},
+        "flushed": {"ms_per_step": ms_flushed,
+                    "value": whole_job_gbs(src_bytes, world, ms_flushed),
+                    "how": "the same steps with a 256 MB L2 flush before each, outside the "
+                           "events (output write-back left outside the timed region)"},
         "encode_gbs": src_bytes / (enc_ms * 1e-3) / 1e9,
         "decode_gbs": src_bytes / (dec_ms * 1e-3) / 1e9,
         "decode_incl_plan_gbs": src_bytes / ((dec_ms + pat_ms) * 1e-3) / 1e9,
@@ -907,7 +955,9 @@ def run_gpu(args):
                      "peak_source": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (int32 issue)",
                      "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_gbs / hbm_peak, "peak_source": peak_src,
-                             "bytes_per_launch": dom_bytes}},
+                             "bytes_per_launch": dom_bytes},
+                     "hbm_frac": achieved_gbs / hbm_peak,
+                     "kernels": per_kernel},
         "e2e": e2e,
         "e2e_u32": e2e_u32,
         "bit_exact": {"round_trip": True, "codewords": W,
@@ -920,7 +970,16 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_extras:
         line["ragged"] = ragged_measure(pkg, dev)
-        line["serving"] = serving_sweep(pkg, count=args.serving_requests)
+        sv = serving_sweep(pkg, count=args.serving_requests)
+        line["serving"] = sv
+        # the serving figures of the metric, at the trace's lowest rate, on one clock
+        # (latency from each request's scheduled arrival, queueing included)
+        line["serving_p50_ms"] = sv["p50_ms"]
+        line["serving_p99_ms"] = sv["p99_ms"]
+        line["serving_gbs"] = sv["achieved_gbs"]
+        line["serving_baseline_p50_ms"] = sv["baseline"]["p50_ms"]
+        line["serving_baseline_p99_ms"] = sv["baseline"]["p99_ms"]
+        line["serving_baseline_gbs"] = sv["baseline"]["achieved_gbs"]
         line["systematic"] = systematic_measure(pkg, dev)
         line["wire"] = wire_measure(pkg, dev)
         line["paper_route"] = paper_route_measure(pkg, dev)
@@ -942,7 +1001,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged and serving runs")
-    ap.add_argument("--serving-requests", type=int, default=300,
+    ap.add_argument("--serving-requests", type=int, default=3000,
                     help="requests replayed per arrival rate in the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":

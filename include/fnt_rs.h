@@ -507,12 +507,16 @@ int fnt_rs_server_release(fnt_rs_server s, uint64_t ticket);
 /* {completed, rejected, arena bytes in use, arena bytes, resident plans}. */
 int fnt_rs_server_stats(fnt_rs_server s, double* out, int cap);
 void fnt_rs_server_destroy(fnt_rs_server s);
-/* Submits reqs[i] at arrival_s[i] seconds (real time) and records latency_ms[i]
- * (-1: refused); *wall_s = duration of the replay. */
+/* Submits reqs[i] once arrival_s[i] seconds (real time) have passed since the
+ * replay's start t0 and records latency_ms[i] counted from that due time
+ * t0 + arrival_s[i] to the moment the dispatcher sees the result (queueing
+ * and a late submission included; -1: refused); *wall_s = duration of the
+ * replay.  fnt_rs_server_poll's latency counts from the submit call. */
 int fnt_rs_server_replay(fnt_rs_server s, const fnt_rs_request* reqs, const double* arrival_s,
                          uint32_t count, double* latency_ms, double* wall_s);
 /* Same trace through the plain path: one request at a time, its plan and
- * pattern built per request, on `stream`. */
+ * pattern built per request, on `stream`; latency on the same clock (due
+ * time to result). */
 int fnt_rs_baseline_replay(const fnt_rs_request* reqs, const double* arrival_s, uint32_t count,
                            double* latency_ms, double* wall_s, void* stream);
 

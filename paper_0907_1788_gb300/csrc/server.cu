@@ -12,10 +12,21 @@
 // seed (uniform 16-bit source symbols for encode, uniform values in
 // [0, 65536] for decode), so host-device copies stay out of the loop.
 //
-// fnt_rs_server_replay feeds a timed trace from a C++ thread (arrivals paced
-// in real time) and records per-request latency; fnt_rs_baseline_replay runs
-// the same trace one request at a time with a plan and pattern built per
-// request, the plain one-launch-per-request path.
+// Locking.  Client calls (submit, poll, release, stats) take only `mu`, which
+// guards the hand-over queues and the published request state; they never
+// wait behind a kernel launch.  The dispatcher owns the arena, the plans, the
+// pattern pools and the stream slots, and launches under `wmu`, a lock that
+// only it and the rare plan-level calls (preplan, destroy) take.  A pattern
+// table whose pinned upload buffer may still be in flight is skipped (its
+// event is queried, never waited on); when no table is free the request stays
+// pending and the dispatcher retries on its next pass.
+//
+// Latency is measured from a request's arrival: the moment submit is called,
+// or for fnt_rs_server_replay the scheduled arrival time t0 + arrival_s[i]
+// (so a submit that runs late still counts from when the request was due), to
+// the moment the dispatcher sees its completion event.  fnt_rs_baseline_replay
+// runs the same trace one request at a time with a plan and pattern built per
+// request, the plain one-launch-per-request path, on the same clock.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -142,7 +153,7 @@ struct Request {
   uint64_t ticket = 0;
   fnt_rs_request r{};
   std::vector<uint32_t> positions;
-  double t_submit = 0, t_start = 0, t_done = 0;
+  double t_arrival = 0, t_start = 0, t_done = 0;
   int status = 0;  // 0 pending, 1 running, 2 done, <0 error
   char* in = nullptr;
   char* out = nullptr;
@@ -169,11 +180,13 @@ struct fnt_rs_server_s {
   size_t ws_bytes_per = 0, pscr_words = 0;
   uint32_t pats_per_plan = 64;
   std::map<std::pair<uint32_t, uint32_t>, PlanRes*> plans;
-  std::mutex mu;
+  std::mutex mu;   // clients: incoming, all, to_release, published request state
+  std::mutex wmu;  // dispatcher state: arena, plans, pools, stream slots
   std::condition_variable cv;
   std::deque<Request*> incoming;
-  std::deque<Request*> pending;
-  std::vector<Request*> running;
+  std::vector<Request*> to_release;  // released by the client, freed by the dispatcher
+  std::deque<Request*> pending;      // dispatcher only
+  std::vector<Request*> running;     // dispatcher only
   std::unordered_map<uint64_t, Request*> all;
   uint64_t next_ticket = 1;
   std::atomic<bool> stop{false};
@@ -231,24 +244,29 @@ static int get_pattern(fnt_rs_server_s* s, Request* r, int si) {
                                                                             : FNT_RS_E_CUDA;
     }
   }
+  // A free table is reusable once its previous build (whose upload reads the
+  // pinned staging buffer) has finished; that is queried, never waited on.
+  auto staged = [](PatEntry* c) {
+    const cudaError_t q = cudaEventQuery(c->built);
+    if (q == cudaErrorNotReady) return false;
+    return q == cudaSuccess;
+  };
   PatEntry* e = nullptr;
   for (auto* c : pr->pool)
-    if (!c->valid && c->refs == 0) {
+    if (!c->valid && c->refs == 0 && staged(c)) {
       e = c;
       break;
     }
   if (!e) {
     for (auto it = pr->lru.rbegin(); it != pr->lru.rend(); ++it)
-      if ((*it)->refs == 0) {
+      if ((*it)->refs == 0 && staged(*it)) {
         e = *it;
         break;
       }
-    if (!e) return 1;  // every table in use: try later
+    if (!e) return 1;  // every table in use or still staging: try later
     pr->lru.remove(e);
     e->valid = false;
   }
-  // the pinned staging may still feed this entry's previous upload
-  if (cudaEventSynchronize(e->built) != cudaSuccess) return FNT_RS_E_CUDA;
   std::memcpy(e->tab.pos_h, key.data(), key.size() * 4);
   cudaStream_t st = s->streams[si];
   if (cudaMemcpyAsync(e->tab.pos_d, e->tab.pos_h, key.size() * 4, cudaMemcpyHostToDevice, st) !=
@@ -272,7 +290,19 @@ static size_t req_out_bytes(const fnt_rs_request& q) {
   return q.op == FNT_RS_OP_ENCODE ? (size_t)q.n * q.W * 4 : (size_t)q.k * q.W * 2;
 }
 
-// Admission: stream slot + arena space.  Returns true if r was started.
+// Sets a request's visible status (1 running, 2 done, < 0 error) under mu.
+static void publish(fnt_rs_server_s* s, Request* r, int status, double t_done = 0) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->status = status;
+  if (status == 2 || status < 0) {
+    r->t_done = t_done > 0 ? t_done : now_s();
+    s->completed += status == 2 ? 1 : 0;
+    if (s->log_done) s->done_log.push_back({r->ticket, (r->t_done - r->t_arrival) * 1e3});
+  }
+}
+
+// Admission: stream slot + arena space.  Returns true if r was started (or
+// failed; its error is then published).  Dispatcher only, under wmu.
 static bool try_start(fnt_rs_server_s* s, Request* r) {
   int si = -1;
   for (uint32_t i = 0; i < s->nstreams; ++i)
@@ -282,7 +312,7 @@ static bool try_start(fnt_rs_server_s* s, Request* r) {
     }
   if (si < 0) return false;
   if (!r->pr && get_plan(s, r->r.n, r->r.k, &r->pr) != FNT_RS_OK) {
-    r->status = FNT_RS_E_CUDA;
+    publish(s, r, FNT_RS_E_CUDA);
     return true;
   }
   r->in_bytes = req_in_bytes(r->r);
@@ -306,7 +336,7 @@ static bool try_start(fnt_rs_server_s* s, Request* r) {
       return false;
     }
     if (rc) {
-      r->status = rc;
+      publish(s, r, rc);
       return true;
     }
   }
@@ -322,36 +352,61 @@ static bool try_start(fnt_rs_server_s* s, Request* r) {
   else
     rc = do_decode_tables(p, r->pat->tab, reinterpret_cast<uint32_t*>(r->in), r->r.W,
                           reinterpret_cast<uint16_t*>(r->out), r->r.W, r->r.W, s->ws[si], st, 0);
-  if (rc) r->status = rc;
   cudaEventRecord(r->done_ev, st);
-  r->status = r->status < 0 ? r->status : 1;
+  publish(s, r, rc ? rc : 1);
   s->busy_bytes += (double)r->r.k * r->r.W * 2;
   return true;
 }
 
-static void finish(fnt_rs_server_s* s, Request* r) {
-  r->t_done = now_s();
+// Completion seen at t_done: frees the slot and pattern reference (and, without
+// kept results, the buffers), then publishes the result.  Dispatcher only.
+static void finish(fnt_rs_server_s* s, Request* r, double t_done) {
   if (r->stream >= 0) s->stream_busy[r->stream] = 0;
   if (r->pat) {
     r->pat->refs--;
     r->pat = nullptr;
   }
-  if (!s->keep_results && r->in) {
-    s->arena.release(r->out, r->out_bytes);
-    s->arena.release(r->in, r->in_bytes);
-    r->in = r->out = nullptr;
+  char* in = nullptr;
+  char* out = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->keep_results) {
+      in = r->in;
+      out = r->out;
+      r->in = r->out = nullptr;
+    }
   }
-  if (r->status == 1) r->status = 2;
-  s->completed++;
-  if (s->log_done) s->done_log.push_back({r->ticket, (r->t_done - r->t_submit) * 1e3});
+  if (in) {
+    s->arena.release(out, r->out_bytes);
+    s->arena.release(in, r->in_bytes);
+  }
+  publish(s, r, 2, t_done);
+}
+
+// Frees what the client released (buffers back to the arena, the record).
+static void reclaim(fnt_rs_server_s* s, std::vector<Request*>& rel) {
+  for (Request* r : rel) {
+    if (r->in) {
+      s->arena.release(r->out, r->out_bytes);
+      s->arena.release(r->in, r->in_bytes);
+    }
+    cudaEventDestroy(r->done_ev);
+    delete r;
+  }
+  rel.clear();
 }
 
 static void worker_loop(fnt_rs_server_s* s) {
   cudaSetDevice(s->dev);
+  std::vector<Request*> rel;
   while (true) {
+    bool stopping = false;
+    // Lock order everywhere: wmu before mu.  pending and running belong to
+    // this thread alone, so reading them here needs neither lock.
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->incoming.empty() && s->pending.empty() && s->running.empty()) {
+      if (s->incoming.empty() && s->to_release.empty() && s->pending.empty() &&
+          s->running.empty()) {
         if (s->stop) break;
         s->cv.wait_for(lk, std::chrono::microseconds(200));
       }
@@ -359,29 +414,35 @@ static void worker_loop(fnt_rs_server_s* s) {
         s->pending.push_back(s->incoming.front());
         s->incoming.pop_front();
       }
-      // completions
+      rel.swap(s->to_release);
+      stopping = s->stop;
+    }
+    {
+      std::lock_guard<std::mutex> wl(s->wmu);
+      reclaim(s, rel);
+      // completions (each is timed when seen)
       for (size_t i = 0; i < s->running.size();) {
         Request* r = s->running[i];
         if (cudaEventQuery(r->done_ev) == cudaSuccess) {
-          finish(s, r);
+          finish(s, r, now_s());
           s->running[i] = s->running.back();
           s->running.pop_back();
         } else {
           ++i;
         }
       }
-      // admissions, in arrival order
+      // admissions, in arrival order; launches run outside mu
       while (!s->pending.empty()) {
         Request* r = s->pending.front();
         if (!try_start(s, r)) break;
         s->pending.pop_front();
-        if (r->status < 0) {
-          r->t_done = now_s();
-          continue;
-        }
+        if (r->status < 0) continue;
         s->running.push_back(r);
       }
-      if (s->stop && s->pending.empty() && s->running.empty() && s->incoming.empty()) break;
+      if (stopping && s->pending.empty() && s->running.empty()) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->incoming.empty()) break;
+      }
     }
     std::this_thread::yield();
   }
@@ -425,12 +486,21 @@ int fnt_rs_server_create(fnt_rs_server* out, size_t budget_bytes, uint32_t nstre
 
 int fnt_rs_server_preplan(fnt_rs_server s, uint32_t n, uint32_t k) {
   if (!s) return FNT_RS_E_ARG;
-  std::lock_guard<std::mutex> lk(s->mu);
+  std::lock_guard<std::mutex> lk(s->wmu);
   PlanRes* pr = nullptr;
   return get_plan(s, n, k, &pr);
 }
 
+static int submit_at(fnt_rs_server s, const fnt_rs_request* req, double t_arrival,
+                     uint64_t* ticket);
+
 int fnt_rs_server_submit(fnt_rs_server s, const fnt_rs_request* req, uint64_t* ticket) {
+  return submit_at(s, req, now_s(), ticket);
+}
+
+// Queues a request that arrived at t_arrival (now_s clock).
+static int submit_at(fnt_rs_server s, const fnt_rs_request* req, double t_arrival,
+                     uint64_t* ticket) {
   if (!s || !req || !ticket) return FNT_RS_E_ARG;
   const fnt_rs_request& q = *req;
   if (q.n < 2 || q.n > kServerMaxN || (q.n & (q.n - 1)) || q.k < 1 || q.k > q.n || q.W == 0 ||
@@ -463,7 +533,7 @@ int fnt_rs_server_submit(fnt_rs_server s, const fnt_rs_request* req, uint64_t* t
     delete r;
     return FNT_RS_E_CUDA;
   }
-  r->t_submit = now_s();
+  r->t_arrival = t_arrival;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;
@@ -484,7 +554,7 @@ int fnt_rs_server_poll(fnt_rs_server s, uint64_t ticket, double* latency_ms) {
   Request* r = it->second;
   if (r->status < 0) return r->status;
   if (r->status != 2) return 0;
-  if (latency_ms) *latency_ms = (r->t_done - r->t_submit) * 1e3;
+  if (latency_ms) *latency_ms = (r->t_done - r->t_arrival) * 1e3;
   return 1;
 }
 
@@ -492,6 +562,7 @@ int fnt_rs_server_drain(fnt_rs_server s) {
   if (!s) return FNT_RS_E_ARG;
   while (true) {
     {
+      std::lock_guard<std::mutex> wl(s->wmu);
       std::lock_guard<std::mutex> lk(s->mu);
       if (s->incoming.empty() && s->pending.empty() && s->running.empty()) return FNT_RS_OK;
     }
@@ -517,27 +588,27 @@ int fnt_rs_server_fetch(fnt_rs_server s, uint64_t ticket, void* h_in, void* h_ou
   return FNT_RS_OK;
 }
 
-// Frees a finished request's buffers and record.
+// Frees a finished request's buffers and record (the dispatcher returns the
+// buffers to the arena on its next pass; the ticket is gone at once).
 int fnt_rs_server_release(fnt_rs_server s, uint64_t ticket) {
   if (!s) return FNT_RS_E_ARG;
-  std::lock_guard<std::mutex> lk(s->mu);
-  auto it = s->all.find(ticket);
-  if (it == s->all.end()) return FNT_RS_E_ARG;
-  Request* r = it->second;
-  if (r->status == 0 || r->status == 1) return FNT_RS_E_ARG;
-  if (r->in) {
-    s->arena.release(r->out, r->out_bytes);
-    s->arena.release(r->in, r->in_bytes);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return FNT_RS_E_ARG;
+    Request* r = it->second;
+    if (r->status == 0 || r->status == 1) return FNT_RS_E_ARG;
+    s->all.erase(it);
+    s->to_release.push_back(r);
   }
-  cudaEventDestroy(r->done_ev);
-  s->all.erase(it);
-  delete r;
+  s->cv.notify_one();
   return FNT_RS_OK;
 }
 
 // {completed, rejected, arena bytes used, arena bytes, plans resident}
 int fnt_rs_server_stats(fnt_rs_server s, double* out, int cap) {
   if (!s || !out) return 0;
+  std::lock_guard<std::mutex> wl(s->wmu);
   std::lock_guard<std::mutex> lk(s->mu);
   const double v[5] = {(double)s->completed, (double)s->rejected, (double)s->arena.used(),
                        (double)s->arena.size(), (double)s->plans.size()};
@@ -558,6 +629,10 @@ void fnt_rs_server_destroy(fnt_rs_server s) {
     cudaEventDestroy(kv.second->done_ev);
     delete kv.second;
   }
+  for (Request* r : s->to_release) {
+    cudaEventDestroy(r->done_ev);
+    delete r;
+  }
   for (auto& kv : s->plans) {
     for (auto* e : kv.second->pool) {
       free_pattern_tables(e->tab);
@@ -575,10 +650,11 @@ void fnt_rs_server_destroy(fnt_rs_server s) {
   delete s;
 }
 
-// Replays a trace: request i is submitted at arrival_s[i] seconds after the
-// start (real time, from this thread); latency_ms[i] receives its latency
-// (negative: rejected).  Returns the wall time of the whole replay in
-// *wall_s.  Results are released as they complete.
+// Replays a trace: request i is due at t0 + arrival_s[i] (real time, t0 =
+// the start of the replay) and submitted by this thread once that time has
+// come; latency_ms[i] receives its latency counted from the due time, queueing
+// and any late submission included (negative: rejected).  Returns the wall
+// time of the whole replay in *wall_s.  Results are released as they complete.
 int fnt_rs_server_replay(fnt_rs_server s, const fnt_rs_request* reqs, const double* arrival_s,
                          uint32_t count, double* latency_ms, double* wall_s) {
   if (!s || (!reqs && count)) return FNT_RS_E_ARG;
@@ -595,7 +671,7 @@ int fnt_rs_server_replay(fnt_rs_server s, const fnt_rs_request* reqs, const doub
     const double t = now_s() - t0;
     while (next < count && arrival_s[next] <= t) {
       uint64_t tk = 0;
-      const int rc = fnt_rs_server_submit(s, &reqs[next], &tk);
+      const int rc = submit_at(s, &reqs[next], t0 + arrival_s[next], &tk);
       if (rc) {
         latency_ms[next] = -1.0;
         ++done;

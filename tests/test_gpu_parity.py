@@ -339,8 +339,8 @@ def test_workload_full_size(pkg, name):
     d_enc = plan.encode(pkg.to_device(src))
     enc_h = pkg.to_host(d_enc)
     rng = np.random.default_rng(cfg.seed)
-    # every codeword: 4 seeded rows by Horner (O(k) each) on a column subset,
-    # two full columns by the oracle
+    # 4 seeded rows by Horner (O(k) each) on every (W/64)-th codeword, two full
+    # codewords by the oracle; the round trip below covers every codeword
     cols = np.sort(rng.choice(cfg.W, 2, replace=False))
     rows = np.sort(rng.choice(cfg.n, 4, replace=False)).astype(np.uint32)
     sub = np.ascontiguousarray(src[:, :: max(1, cfg.W // 64)])

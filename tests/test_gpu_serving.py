@@ -101,3 +101,27 @@ def test_budget_and_replay(pkg):
         pkg.fnt_rs_server_destroy(srv)
     lat, wall = pkg.fnt_rs_baseline_replay(reqs[:16], arrivals[:16])
     assert (lat >= 0).all()
+
+
+def test_replay_latency_counts_from_scheduled_arrival(pkg):
+    # Every request is due at once: the last result must arrive about one wall
+    # time after the start, so the largest latency (counted from the due time,
+    # queueing and late submission included) is close to the replay's wall time,
+    # and no latency can be below the shortest possible queue wait of zero.
+    reqs = _trace(32)
+    arrivals = [0.0] * len(reqs)
+    srv = pkg.fnt_rs_server_create(1 << 30, nstreams=4, keep_results=False)
+    try:
+        for n, k in {(q["n"], q["k"]) for q in reqs}:
+            pkg.fnt_rs_server_preplan(srv, n, k)
+        lat, wall = pkg.fnt_rs_server_replay(srv, reqs, arrivals)
+    finally:
+        pkg.fnt_rs_server_destroy(srv)
+    assert (lat >= 0).all()
+    assert lat.max() <= wall * 1e3 + 1.0
+    assert lat.max() >= 0.8 * wall * 1e3 - 1.0
+    blat, bwall = pkg.fnt_rs_baseline_replay(reqs, arrivals)
+    assert (blat >= 0).all()
+    # one request at a time from a common due time: latencies grow in trace order
+    assert np.all(np.diff(blat) >= 0)
+    assert blat.max() <= bwall * 1e3 + 1.0
