@@ -182,22 +182,41 @@ int launch_encode_tma_t(const KArgs& a, const uint32_t* twc, int rows_staged, in
 namespace fntrs {
 constexpr int decode_tma_max_rows(int L) { return L <= 256 ? L : L / 2; }
 
+// Number of WT-wide tiles kept when the last round of a one-CTA-per-tile
+// launch (nwide tiles over `resident` CTAs at a time) is cut into half-width
+// tiles: only when the remainder r fills at most half the CTAs, so that its
+// 2r half tiles still form a single round.
+inline int tail_full_tiles(int nwide, int resident, int wt) {
+  if (wt < 2 || resident <= 0) return nwide;
+  const int r = nwide % resident;
+  return (r != 0 && 2 * r <= resident) ? nwide - r : nwide;
+}
+
 template <class S, int WT, int NT, bool HALF>
 int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
   auto kern = k_decode_tma<S, WT, NT, HALF>;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
   const int smem = work + t.rows_staged * WT * 4 + kSchedBytes;
   static bool done[64] = {};
+  static int occ[64] = {};  // CTAs resident per SM at the largest stage
   int dev = 0;
   cudaGetDevice(&dev);
   if (!done[dev & 63]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             work + decode_tma_max_rows(S::L) * WT * 4 + kSchedBytes) != cudaSuccess)
+    const int max_smem = work + decode_tma_max_rows(S::L) * WT * 4 + kSchedBytes;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
+        cudaSuccess)
       return -1;
+    int o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, max_smem) != cudaSuccess)
+      o = 1;
+    occ[dev & 63] = o > 0 ? o : 1;
     done[dev & 63] = true;
   }
-  kern<<<t.grid, NT, smem, st>>>(a, t.pat32, t.rows_staged, t.box_rows,
-                                 *static_cast<const CUtensorMap*>(t.map));
+  const int nwide = (a.W + WT - 1) / WT;
+  const int nfull = tail_full_tiles(nwide, t.sms * occ[dev & 63], WT);
+  const int grid = nfull + 2 * (nwide - nfull);  // one CTA per tile (see clc_take)
+  kern<<<grid, NT, smem, st>>>(a, t.pat32, t.rows_staged, t.box_rows, nfull,
+                               *static_cast<const CUtensorMap*>(t.map));
   count_launch();
   return 0;
 }

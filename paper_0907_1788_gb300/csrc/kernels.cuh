@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if constexpr (S::NP == 3) {
         dif_mid<S, WT, NT, false>(work, a.twf + S::TW2_OFF);
-        __syncthreads();
+        mid_last_sync<S, WT, NT>();  // the last pass reads only its group's blocks
       }
       // last pass -> encoded rows cc + C*j
       {
@@ -658,6 +658,7 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
 // staged [k][WT] tile through pat32[z] = (row << 17) | c_z (c_z = 0: unused).
 // smem: work (Lay WORDS u32) | stage (rows_staged * WT u32) | mbarrier.
 // ---------------------------------------------------------------------------
+// (WT = the stage's row stride; `stage` may point at a column inside the row)
 template <int WT>
 struct LoadStaged {
   const uint32_t* stage;
@@ -694,7 +695,7 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
   freed();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
-    __syncthreads();
+    mid_last_sync<S, WT, NT>();  // the last pass reads only its group's blocks
   }
   // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
   {
@@ -723,9 +724,11 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
       for (int q = 0; q < R; ++q) base[bitrev(q, B) * WT] = x[q];
     }
   }
-  __syncthreads();
   if constexpr (S::NP == 3) {
+    mid_last_sync<S, WT, NT>();
     dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
+    __syncthreads();
+  } else {
     __syncthreads();
   }
   // last D2 pass * ahat + first D3 pass
@@ -752,17 +755,23 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
   __syncthreads();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
-    __syncthreads();
+    mid_last_sync<S, WT, NT>();
   }
   dif_last_sel<S, WT, NT, true, HALF>(sm, store);
 }
 
+// Tiles: the first `nfull` tiles are WT codewords wide; the columns after them
+// are cut into tiles of WT/2 codewords (two per WT-wide TMA box), so that the
+// last round of tiles, which would otherwise keep only part of the SMs busy,
+// is spread over twice as many CTAs.  With nfull = ceil(W / WT) every tile is
+// WT wide.
 template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
-                 const __grid_constant__ CUtensorMap trecv) {
+                 int nfull, const __grid_constant__ CUtensorMap trecv) {
   static_assert(S::NP >= 2, "");
   using Y = Lay<S, WT>;
+  constexpr int WH = WT >= 2 ? WT / 2 : 1;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
   extern __shared__ __align__(128) uint4 smem_raw[];
   __shared__ int s_next;
@@ -771,7 +780,11 @@ __global__ void __launch_bounds__(NT, 1)
   uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)rows_staged * WT);
   uint64_t* cbar = bar + 1;
   uint4* resp = reinterpret_cast<uint4*>(bar + 2);
-  const int ntiles = (a.W + WT - 1) / WT;
+  const int nwide = (a.W + WT - 1) / WT;
+  if (WT < 2 || nfull > nwide) nfull = nwide;
+  const int ntiles = nfull + 2 * (nwide - nfull);
+  // x coordinate of the WT-wide box that holds tile t's columns
+  auto box_x = [&](int t) { return t < nfull ? t * WT : (nfull + ((t - nfull) >> 1)) * WT; };
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
   int tile = blockIdx.x;
@@ -783,13 +796,34 @@ __global__ void __launch_bounds__(NT, 1)
   if (threadIdx.x == 0 && tile < ntiles) {
     mbar_expect_tx(bar, tx_bytes);
     for (int bx = 0; bx < nbox; ++bx)
-      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, tile * WT, bx * box_rows, bar);
+      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(tile), bx * box_rows, bar);
     clc_request(resp, cbar);
   }
   uint32_t parity = 0, cphase = 0;
   bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
   LoadStaged<WT> load{stage, pat32, 0u};
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
+  StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
+  auto freed = [&]() {
+    if (threadIdx.x == 0) {
+      // the stage is free: take over a pending CTA's tile and prefetch it
+      int nxt = clc_take(resp, cbar, cphase);
+      pending = false;
+      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+      if (nxt >= 0 && nxt < ntiles) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, tx_bytes);
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(nxt), bx * box_rows,
+                      bar);
+        clc_request(resp, cbar);
+        pending = true;
+      } else {
+        nxt = ntiles;
+      }
+      s_next = nxt;
+    }
+  };
   while (tile < ntiles) {
     const bool ok = mbar_wait(bar, parity);
     if (__syncthreads_or(!ok)) {
@@ -801,32 +835,27 @@ __global__ void __launch_bounds__(NT, 1)
       return;
     }
     parity ^= 1u;
-    store.col0 = tile * WT;
-    decode_staged_tile<S, WT, NT, HALF>(sm, load, store, a, [&]() {
-      if (threadIdx.x == 0) {
-        // the stage is free: take over a pending CTA's tile and prefetch it
-        int nxt = clc_take(resp, cbar, cphase);
-        pending = false;
-        if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
-        if (nxt >= 0 && nxt < ntiles) {
-          fence_proxy_async();
-          mbar_expect_tx(bar, tx_bytes);
-          for (int bx = 0; bx < nbox; ++bx)
-            tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, nxt * WT, bx * box_rows,
-                        bar);
-          clc_request(resp, cbar);
-          pending = true;
-        } else {
-          nxt = ntiles;
-        }
-        s_next = nxt;
+    if constexpr (WT >= 2) {
+      if (tile >= nfull) {
+        // a half tile: columns (tile - nfull) & 1 of its box, WH codewords
+        const int h = tile - nfull;
+        LoadStaged<WT> lh{stage + (h & 1) * WH, pat32, load.vmax};
+        store_h.col0 = nfull * WT + h * WH;
+        decode_staged_tile<S, WH, NT, HALF>(sm, lh, store_h, a, freed);
+        load.vmax = lh.vmax;
+        __syncthreads();
+        tile = s_next;
+        continue;
       }
-    });
+    }
+    store.col0 = tile * WT;
+    decode_staged_tile<S, WT, NT, HALF>(sm, load, store, a, freed);
     __syncthreads();
     tile = s_next;
   }
   if (load.vmax > 65536u) atomicOr(a.status, ST_RANGE);
   store.flush();
+  store_h.flush();
 }
 
 // ---------------------------------------------------------------------------

@@ -819,7 +819,7 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   t.pat32 = sl.pat32;
   t.rows_staged = rows_staged;
   t.box_rows = box_rows;
-  t.grid = (int)((W + WT - 1) / WT);  // one CTA per tile (see clc_take)
+  t.sms = p->sms;
   t.map = &map;
   if (launch_decode_tma(L, a, t, st) != 0) return 1;
   return cuda_ok(cudaGetLastError());

@@ -73,7 +73,8 @@ int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cuda
 // TMA-staged decode (n = L <= tile limit, k <= n/2, packed rows).
 struct TmaDecodeArgs {
   const uint32_t* pat32;
-  int rows_staged, box_rows, grid;
+  int rows_staged, box_rows;
+  int sms;          // SMs of the device (the launch sizes its last round of tiles by it)
   const void* map;  // CUtensorMap*
 };
 int launch_decode_tma(int L, const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st);

@@ -102,6 +102,32 @@ __device__ __forceinline__ void bitrev_regs(uint32_t* x) {
 }
 
 // ---------------------------------------------------------------------------
+// Barrier between the middle pass and the last pass of a 3-pass schedule (in
+// either direction).  With R2 = RL both passes give the S1 slots of one middle
+// block b to the same G = (S1 / R2) * WT consecutive tasks, and task t runs on
+// thread t mod NT; when G is a multiple of the warp size that divides NT, the
+// threads that write a block are the threads that read it, so only their
+// group of G threads (thread index / G) has to meet: one warp (syncwarp) or a
+// named barrier of G threads (ids 1..NT/G; id 0 is __syncthreads).  Otherwise
+// the whole CTA meets.
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT>
+__device__ __forceinline__ void mid_last_sync() {
+  constexpr int G = (S::NP == 3) ? (S::S1 / S::R2) * WT : 0;
+  if constexpr (S::NP == 3 && S::R2 == S::RL && G % 32 == 0 && G > 0 && NT % G == 0 &&
+                NT / G <= 15) {
+    if constexpr (G == 32) {
+      __syncwarp();
+    } else {
+      const int id = 1 + (int)threadIdx.x / G;
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(G) : "memory");
+    }
+  } else {
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Pass building blocks.  Task loops run over (group g, codeword c), c fastest.
 // ---------------------------------------------------------------------------
 

@@ -163,6 +163,26 @@ def test_decode_random_received_matches_oracle(pkg, n, k, W):
     assert st == (pkg.E_RANGE if flag else 0)
 
 
+@pytest.mark.parametrize("n,k,W", [(8192, 4096, 643), (4096, 2048, 1285), (8192, 3000, 645),
+                                   (512, 256, 9927)])
+def test_decode_full_and_half_width_tiles(pkg, n, k, W):
+    # W large enough for a full round of full-width tiles with a short last
+    # round, which the staged decode cuts into half-width tiles (and a ragged
+    # last tile): every codeword must come back, and random received words
+    # must match the oracle in columns of every kind of tile
+    src = synth.source(7 * n + W, k, W)
+    plan = pkg.Plan(n, k)
+    enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+    pos = synth.received_positions(n, synth.erased_uniform(n + W, n, k))
+    assert np.array_equal(_dec(pkg, plan, np.ascontiguousarray(enc[pos]), pos), src)
+    assert plan.status() == 0
+    v = synth.received_uniform(W + k, k, W)
+    got = _dec(pkg, plan, v, pos)
+    cols = sorted({0, 1, W // 2, W - 9, W - 6, W - 5, W - 4, W - 3, W - 1})
+    want, flag = oracle.decode(np.ascontiguousarray(v[:, cols]), pos, n, k)
+    assert np.array_equal(got[:, cols], want)
+
+
 @pytest.mark.parametrize("n,k,W", [(16384, 8192, 8), (16384, 12000, 5), (65536, 32768, 3),
                                    (32768, 30000, 3), (32768, 16384, 4), (32768, 10000, 3)])
 def test_decode_split_sizes_sampled(pkg, n, k, W):
