@@ -824,17 +824,25 @@ def run_gpu(args):
     assert round_trip_ok(), "round trip failed (flushed)"
 
     # per-phase times (and the dominant kernel's duration for the roofline) from
-    # the same steps run serially
-    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_((i + 3) & 0xFF)
-        step_serial(args.warmup + args.steps + i, sev[i])
-    torch.cuda.synchronize()
-    t_enc = [e[0].elapsed_time(e[1]) for e in sev]
-    t_pat = [e[1].elapsed_time(e[2]) for e in sev]
-    t_dec = [e[2].elapsed_time(e[3]) for e in sev]
+    # the same steps run serially, back to back over the rotating buffers like
+    # the timed steps (each kernel pays the write-back of the dirty lines the
+    # kernel before it left in L2); then once more with L2 flushed before each
+    # step, where every kernel starts from an L2 full of dirty flush data
+    def serial_pass(with_flush, base):
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            if with_flush:
+                flush.fill_((i + 3) & 0xFF)
+            step_serial(base + i, sev[i])
+        torch.cuda.synchronize()
+        return ([e[0].elapsed_time(e[1]) for e in sev], [e[1].elapsed_time(e[2]) for e in sev],
+                [e[2].elapsed_time(e[3]) for e in sev])
+
+    t_enc, t_pat, t_dec = serial_pass(False, args.warmup + args.steps)
     ms_serial = (sum(t_enc) + sum(t_pat) + sum(t_dec)) / args.steps
+    f_enc, f_pat, f_dec = serial_pass(True, args.warmup + 2 * args.steps)
     assert round_trip_ok(), "round trip failed (serial)"
 
     src_bytes = k * W * 2
@@ -940,7 +948,15 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "autotune": tuned,
         "breakdown_ms": {"encode": enc_ms, "plan": pat_ms, "decode": dec_ms,
-                         "serial_step": ms_serial},
+                         "serial_step": ms_serial,
+                         "how": "the step's three calls one after another on one stream, "
+                                "back to back over the rotating buffers (no flush); means"},
+        "breakdown_flushed_ms": {"encode": statistics.mean(f_enc),
+                                 "plan": statistics.mean(f_pat),
+                                 "decode": statistics.mean(f_dec),
+                                 "how": "the same with a 256 MB L2 flush before each step "
+                                        "(the flush's dirty lines are written back during "
+                                        "the kernels)"},
         "flushed": {"ms_per_step": ms_flushed,
                     "value": whole_job_gbs(src_bytes, world, ms_flushed),
                     "how": "the same steps with a 256 MB L2 flush before each, outside the "

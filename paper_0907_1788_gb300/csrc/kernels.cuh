@@ -420,10 +420,13 @@ __global__ void __launch_bounds__(NT, 1)
                 }
               }
             } else {
+              // streaming stores (evict first): the encoded words are not read
+              // again here, so their lines leave L2 while this kernel still
+              // computes instead of being written back during the next kernel
               uint32_t* o = out + (size_t)(cc + C * S::natural(b * RL)) * ld + col;
               const size_t step = (size_t)C * (S::L / RL) * ld;
 #pragma unroll
-              for (int q = 0; q < RL; ++q) o[bitrev(q, BL) * step] = m_to_p(x[q]);
+              for (int q = 0; q < RL; ++q) __stcs(o + bitrev(q, BL) * step, m_to_p(x[q]));
             }
           }
         }
@@ -512,10 +515,11 @@ struct StoreOut16 {
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
     if (col >= W || j >= k) return;
+    // streaming stores: the decoded symbols are not read again by this kernel
     if (out32)
-      out32[(size_t)j * ld + col] = m_to_p(v);
+      __stcs(out32 + (size_t)j * ld + col, m_to_p(v));
     else
-      out[(size_t)j * ld + col] = to_symbol(v, bad);
+      __stcs(out + (size_t)j * ld + col, to_symbol(v, bad));
   }
   __device__ __forceinline__ void flush() const {
     if (bad > 65535u) atomicOr(status, ST_RANGE);
