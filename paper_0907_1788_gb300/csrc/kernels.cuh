@@ -178,7 +178,57 @@ __device__ __forceinline__ uint16_t to_symbol(uint32_t v, uint32_t& bad) {
 }
 
 // Local pass of a split transform (n = C * L): spectrum index j of block j1
-// is row j1 + C*j of the full transform.
+// is row j1 + C*j of the full transform, stored according to MODE (kargs.h).
+// With CG the pointwise tables are read through L2 only (written by other CTAs
+// of the same launch).
+template <int MODE, bool CG = false>
+__device__ __forceinline__ void local_store(const KArgs& a, int j1, int j, int col, uint32_t v,
+                                            uint32_t& bad) {
+  const size_t row = (size_t)j1 + (size_t)a.C * j;
+  if constexpr (MODE == LM_ENC || MODE == LM_FNT) {
+    if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
+    const size_t orow =
+        a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
+    if (MODE == LM_ENC && a.wire)
+      WireOut::make(a).put((uint32_t)orow, col, m_to_p(v));
+    else
+      static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
+  } else if constexpr (MODE == LM_WORK) {
+    if ((int)row < a.out_limit) static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
+  } else if constexpr (MODE == LM_WORK_AHAT) {
+    static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(v, ld_tab<CG>(a.ahat + row));
+  } else if constexpr (MODE == LM_OUT16) {
+    if ((int)row < a.out_limit) {
+      if (a.scale != 1u) v = m_mul(v, a.scale);
+      if (a.out32)
+        static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
+      else
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
+    }
+  } else if constexpr (MODE == LM_SPLIT) {
+    if ((int)row < a.h)
+      static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
+    else if ((int)row < a.out_limit)
+      static_cast<uint32_t*>(a.out3)[(row - a.h) * a.ld_work + col] = v;
+  } else if constexpr (MODE == LM_X_PARTIAL) {
+    const uint32_t vp = m_to_p(v);
+    static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(vp, ld_tab<CG>(a.ahat + row));
+    static_cast<uint32_t*>(a.out3)[row * a.ld_work + col] = m_mul(vp, ld_tab<CG>(a.ahat2 + row));
+  } else if constexpr (MODE == LM_ACCUM) {
+    uint32_t* p = static_cast<uint32_t*>(a.out3) + row * a.ld_work + col;
+    *p = m_add(*p, m_mul(v, ld_tab<CG>(a.ahat + row)));
+  } else if constexpr (MODE == LM_OUT16_ADD) {
+    if ((int)row < a.out_limit) {
+      if ((int)row >= a.h)
+        v = m_add(v, static_cast<const uint32_t*>(a.in2)[(row - a.h) * a.ld_work + col]);
+      if (a.out32)
+        static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
+      else
+        static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
+    }
+  }
+}
+
 template <int WT, int MODE>
 struct StoreLocal {
   KArgs a;
@@ -190,48 +240,36 @@ struct StoreLocal {
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
     if (col >= a.W) return;
-    const size_t row = (size_t)j1 + (size_t)a.C * j;
-    if constexpr (MODE == LM_ENC || MODE == LM_FNT) {
-      if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
-      const size_t orow =
-          a.row_mul == 1u ? row : ((a.row_mul * (uint32_t)row) & (uint32_t)(a.n - 1));
-      if (MODE == LM_ENC && a.wire)
-        WireOut::make(a).put((uint32_t)orow, col, m_to_p(v));
-      else
-        static_cast<uint32_t*>(a.out)[orow * a.ld_out + col] = m_to_p(v);
-    } else if constexpr (MODE == LM_WORK) {
-      if ((int)row < a.out_limit) static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
-    } else if constexpr (MODE == LM_WORK_AHAT) {
-      static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(v, __ldg(a.ahat + row));
-    } else if constexpr (MODE == LM_OUT16) {
-      if ((int)row < a.out_limit) {
-        if (a.scale != 1u) v = m_mul(v, a.scale);
-        if (a.out32)
-          static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
-        else
-          static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
-      }
-    } else if constexpr (MODE == LM_SPLIT) {
-      if ((int)row < a.h)
-        static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = v;
-      else if ((int)row < a.out_limit)
-        static_cast<uint32_t*>(a.out3)[(row - a.h) * a.ld_work + col] = v;
-    } else if constexpr (MODE == LM_X_PARTIAL) {
-      const uint32_t vp = m_to_p(v);
-      static_cast<uint32_t*>(a.out2)[row * a.ld_work + col] = m_mul(vp, __ldg(a.ahat + row));
-      static_cast<uint32_t*>(a.out3)[row * a.ld_work + col] = m_mul(vp, __ldg(a.ahat2 + row));
-    } else if constexpr (MODE == LM_ACCUM) {
-      uint32_t* p = static_cast<uint32_t*>(a.out3) + row * a.ld_work + col;
-      *p = m_add(*p, m_mul(v, __ldg(a.ahat + row)));
-    } else if constexpr (MODE == LM_OUT16_ADD) {
-      if ((int)row < a.out_limit) {
-        if ((int)row >= a.h)
-          v = m_add(v, static_cast<const uint32_t*>(a.in2)[(row - a.h) * a.ld_work + col]);
-        if (a.out32)
-          static_cast<uint32_t*>(a.out32)[row * a.ld_out + col] = m_to_p(v);
-        else
-          static_cast<uint16_t*>(a.out)[row * a.ld_out + col] = to_symbol(v, bad);
-      }
+    local_store<MODE>(a, j1, j, col, v, bad);
+  }
+  __device__ __forceinline__ void flush() const {
+    if (bad > 65535u) atomicOr(a.status, ST_RANGE);
+  }
+};
+
+// The same with the mode chosen at run time (a.mode; uniform over the CTA), for
+// the persistent kernel, which runs every mode through one tile body.
+template <int WT, bool CG>
+struct StoreLocalRT {
+  KArgs a;
+  int col0, j1;
+  uint32_t bad;
+  static __device__ __forceinline__ StoreLocalRT make(const KArgs& a, int tx, int ty) {
+    return StoreLocalRT{a, tx * WT, ty, 0u};
+  }
+  __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
+    const int col = col0 + c;
+    if (col >= a.W) return;
+    switch (a.mode) {
+      case LM_ENC: local_store<LM_ENC, CG>(a, j1, j, col, v, bad); break;
+      case LM_FNT: local_store<LM_FNT, CG>(a, j1, j, col, v, bad); break;
+      case LM_WORK: local_store<LM_WORK, CG>(a, j1, j, col, v, bad); break;
+      case LM_WORK_AHAT: local_store<LM_WORK_AHAT, CG>(a, j1, j, col, v, bad); break;
+      case LM_OUT16: local_store<LM_OUT16, CG>(a, j1, j, col, v, bad); break;
+      case LM_SPLIT: local_store<LM_SPLIT, CG>(a, j1, j, col, v, bad); break;
+      case LM_X_PARTIAL: local_store<LM_X_PARTIAL, CG>(a, j1, j, col, v, bad); break;
+      case LM_ACCUM: local_store<LM_ACCUM, CG>(a, j1, j, col, v, bad); break;
+      default: local_store<LM_OUT16_ADD, CG>(a, j1, j, col, v, bad); break;
     }
   }
   __device__ __forceinline__ void flush() const {
@@ -442,14 +480,11 @@ __global__ void __launch_bounds__(NT, 1)
 // column, the radix-C DFT over rows i1*L + i2 followed by the twiddle
 // r_n^(+-i2*j1); result row j1*L + i2 of the workspace matrix out2.
 // ---------------------------------------------------------------------------
-template <int C, bool INV, int LOADM>
-__global__ void __launch_bounds__(256) k_cross(KArgs a) {
-  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
-  const int col = (int)(t % a.W);
-  const long long i2l = t / a.W;
-  if (i2l >= a.L) return;
-  const int i2 = (int)i2l;
-  uint32_t bad = 0u;
+// One (i2, column) of the cross pass.  With CG the pattern table and the
+// received words are read through L2 only (they may have been written by
+// other CTAs of the same launch).  `bad` collects received values above 65536.
+template <int C, bool INV, int LOADM, bool CG = false>
+__device__ __forceinline__ void cross_one(const KArgs& a, int i2, int col, uint32_t& bad) {
   uint32_t x[C];
 #pragma unroll
   for (int q = 0; q < C; ++q) {
@@ -465,17 +500,17 @@ __global__ void __launch_bounds__(256) k_cross(KArgs a) {
       x[q] = row < a.row_limit ? static_cast<const uint32_t*>(a.in)[(size_t)r * a.ld_in + col]
                                : 0u;
     } else {
-      const uint2 e = __ldg(a.pat + row);
+      const uint2 e = ld_tab<CG>(a.pat + row);
       uint32_t v = 0u;
       if (e.y != 0u) {
         const size_t rr = a.slots ? (size_t)row : (size_t)e.x;
-        v = static_cast<const uint32_t*>(a.in)[rr * a.ld_in + col];
+        const uint32_t* src = static_cast<const uint32_t*>(a.in) + rr * a.ld_in + col;
+        v = CG ? __ldcg(src) : *src;
       }
       bad |= v > 65536u ? 1u : 0u;
       x[q] = m_mul(v, e.y);
     }
   }
-  if (bad) atomicOr(a.status, ST_RANGE);
   dft_reg<C, INV>(x);
   const uint32_t* pw = INV ? a.powi : a.powf;
   constexpr int B = ilog2(C);
@@ -487,6 +522,17 @@ __global__ void __launch_bounds__(256) k_cross(KArgs a) {
     if (j1 != 0) v = m_mul(v, __ldg(pw + (((long long)i2 * j1) & (a.n - 1))));
     out[((size_t)j1 * a.L + i2) * a.ld_work + col] = v;
   }
+}
+
+template <int C, bool INV, int LOADM>
+__global__ void __launch_bounds__(256) k_cross(KArgs a) {
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  const int col = (int)(t % a.W);
+  const long long i2l = t / a.W;
+  if (i2l >= a.L) return;
+  uint32_t bad = 0u;
+  cross_one<C, INV, LOADM>(a, (int)i2l, col, bad);
+  if (bad) atomicOr(a.status, ST_RANGE);
 }
 
 // ---------------------------------------------------------------------------

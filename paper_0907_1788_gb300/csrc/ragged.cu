@@ -4,13 +4,15 @@
 // Every group is a full round trip: encode its source (Sec. II.B, e = FNT of
 // the zero-padded source), build its pattern tables (steps 1-3), decode every
 // codeword from the encoded matrix used as the receiver's slot buffer
-// (steps 4-6).  Groups with 256 <= n <= 8192 (default root) all run in one
-// launch of the ragged persistent kernel (ragged_kernel.cu), each with its own
-// pattern tables and build scratch.  The other groups (longer codes, through
-// the split transforms) keep per-group launches: groups sharing (n, k) share
-// one plan and run in order on one stream, and plan classes are spread over
-// several streams by estimated work.  The persistent kernel's stream and the
-// others are captured into a single graph.
+// (steps 4-6).  Groups with n >= 256 and the default root (every length of
+// the survey's ragged batch, up to 65536) all run in one launch of the ragged
+// persistent kernel (ragged_kernel.cu), each with its own pattern tables and
+// build scratch; the split-transform work items of the longest codes use a
+// scratch area per CTA.  Other groups (n < 256, another root, or the
+// product-tree pattern route) keep per-group launches: groups sharing (n, k)
+// share one plan and run in order on one stream, and plan classes are spread
+// over several streams by estimated work.  The persistent kernel's stream and
+// the others are captured into a single graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +38,13 @@ struct RaggedGroup {
   uint32_t* scratch = nullptr;  // its own pattern-build scratch (persistent decode groups)
 };
 
+// Words of a persistent decode group's pattern-build scratch: the one-launch
+// build's digit convolutions and tail buffers, or for a long code (n >= 32768)
+// indicator, spectrum, per-digit products, convolutions and tail buffers.
+inline size_t ragged_plan_scratch_words(size_t n, size_t D) {
+  return ragged_long_plan((int)n) ? (2 * D + 8) * n : n * D + 6 * n;
+}
+
 }  // namespace fntrs
 
 using namespace fntrs;
@@ -59,6 +68,7 @@ struct fnt_rs_ragged_s {
   size_t counter_bytes = 0;
   int grid = 0;
   int npersistent = 0;
+  uint32_t* cta_scratch = nullptr;  // split-transform buffers of the persistent CTAs
   int tuned = 0;  // plans whose schedules the autotuner picked
 };
 
@@ -81,8 +91,24 @@ static void free_group(RaggedGroup& rg) {
 }
 
 static bool persistent_eligible(const fnt_rs_plan_s* p) {
-  return p->n >= (uint32_t)kRaggedMinL && p->n <= (uint32_t)kRaggedMaxL && p->u == 1 &&
-         !p->plan_tree && fused_plan_applies(p);
+  if (p->n < (uint32_t)kRaggedMinL || p->n > (uint32_t)kRaggedMaxL || p->u != 1 || p->plan_tree)
+    return false;
+  // short codes: the one-launch pattern build's digit items
+  return ragged_long_plan((int)p->n) || tile_ops((int)p->n).plan_fused != nullptr;
+}
+
+// Words of split-transform scratch one persistent CTA needs for this group.
+static size_t cta_scratch_words(const RaggedGroup& rg) {
+  const fnt_rs_plan_s* p = rg.plan;
+  const int n = (int)p->n;
+  size_t w = 0;
+  if (ragged_split_enc(n)) w = std::max(w, (size_t)n * kRaggedSplitWT);
+  if (rg.g.positions) {
+    if (ragged_split_dec(n, p->blocked))
+      w = std::max(w, (size_t)(p->blocked ? 4 : 2) * n * kRaggedSplitWT);
+    if (ragged_long_plan(n) && n > kTileMaxL) w = std::max(w, (size_t)2 * n);
+  }
+  return w;
 }
 
 // Device group record of a persistent group (same arguments as the per-group
@@ -97,6 +123,10 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   d.has_plan = g.positions ? 1 : 0;
   d.enc_tiles = (int)((g.W + ragged_wt_enc(n) - 1) / ragged_wt_enc(n));
   d.enc_need = d.enc_tiles;
+  d.split_enc = ragged_split_enc(n) ? 1 : 0;
+  d.split_dec = ragged_split_dec(n, p->blocked) ? 1 : 0;
+  d.long_plan = ragged_long_plan(n) ? 1 : 0;
+  d.C = n > kLocalL ? n / kLocalL : 1;
   KArgs& e = d.enc;
   e.in = g.src;
   e.ld_in = g.ld_src;
@@ -111,6 +141,18 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   e.twi = p->tn.twi;
   e.powf = p->tn.powf;
   e.row_mul = p->uinv;
+  if (d.split_enc) {
+    KArgs& x = d.xenc;  // the split encode's cross and local passes
+    x.n = n;
+    x.k = k;
+    x.L = kLocalL;
+    x.C = d.C;
+    x.powf = p->tn.powf;
+    x.powi = p->tn.powi;
+    x.twf = p->tl.twf;
+    x.twi = p->tl.twi;
+    x.status = p->status;
+  }
   if (!g.positions) return d;
   KArgs& a = d.dec;
   a.slots = 1;
@@ -130,6 +172,61 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   a.C = 1;
   a.twf = p->tn.twf;
   a.twi = p->tn.twi;
+  if (d.split_dec) {
+    KArgs& x = d.xdec;  // the split decode's passes (received rows = the slot buffer)
+    x = a;
+    x.L = kLocalL;
+    x.C = d.C;
+    x.powf = p->tn.powf;
+    x.powi = p->tn.powi;
+    x.twf = p->tl.twf;
+    x.twi = p->tl.twi;
+  }
+  if (d.long_plan) {
+    // scratch: ind [n] | spec [n] | prod [D][n] | conv [n][D] | aval | coef [n] | M2, E2 [n][2]
+    const size_t D = (size_t)p->lg_D;
+    LongPlanDev& lp = d.lp;
+    lp.ind = rg.scratch;
+    lp.spec = lp.ind + n;
+    lp.prod = lp.spec + n;
+    uint32_t* conv = lp.prod + D * n;
+    lp.aval = conv + D * n;
+    lp.coef = lp.aval + n;
+    lp.M2 = lp.coef + n;
+    lp.E2 = lp.M2 + 2 * (size_t)n;
+    for (KArgs* c : {&d.colf, &d.coli}) {  // one-column transforms of length n
+      c->n = n;
+      c->C = 1;
+      c->status = p->status;
+      if (n <= kTileMaxL) {
+        c->L = n;
+        c->twf = p->tn.twf;
+        c->twi = p->tn.twi;
+      } else {
+        c->L = kLocalL;
+        c->C = d.C;
+        c->powf = p->tn.powf;
+        c->powi = p->tn.powi;
+        c->twf = p->tl.twf;
+        c->twi = p->tl.twi;
+      }
+    }
+    PlanArgs& pa = d.plan;
+    pa.k = k;
+    pa.D = p->lg_D;
+    pa.b = p->lg_b;
+    pa.ninv = p->ninv;
+    pa.pos = rg.tab.pos_d;
+    pa.ghat = p->ghat;
+    pa.exp3 = p->exp3;
+    pa.conv = conv;
+    pa.pat = rg.tab.pat;
+    pa.pat32 = rg.tab.pat32;
+    pa.aval = p->blocked ? lp.aval : nullptr;
+    pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
+    pa.done = rg.tab.done;
+    return d;
+  }
   // scratch: conv [n][D] | aval [n] | coef [n] | halves [n][2] | E [n][2]
   uint32_t* conv = rg.scratch;
   uint32_t* aval = conv + (size_t)n * p->lg_D;
@@ -201,6 +298,7 @@ void fnt_rs_ragged_destroy(fnt_rs_ragged r) {
   cudaFree(r->d_groups);
   cudaFree(r->d_items);
   cudaFree(r->d_counters);
+  cudaFree(r->cta_scratch);
   for (void* w : r->ws) cudaFree(w);
   for (auto s : r->streams) cudaStreamDestroy(s);
   for (auto e : r->joins) cudaEventDestroy(e);
@@ -258,9 +356,8 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     if (!rg.persistent) continue;
     pers.push_back(i);
     if (rg.g.positions) {
-      const size_t n = rg.plan->n;
-      if (cudaMalloc(&rg.scratch, (n * rg.plan->lg_D + 6 * n) * 4) != cudaSuccess)
-        return fail(FNT_RS_E_CUDA);
+      const size_t words = ragged_plan_scratch_words(rg.plan->n, (size_t)rg.plan->lg_D);
+      if (cudaMalloc(&rg.scratch, words * 4) != cudaSuccess) return fail(FNT_RS_E_CUDA);
     }
   }
   if (!pers.empty()) {
@@ -283,6 +380,9 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
       if (pers[gi] == stall) dg.back().enc_need += 1;
       for (int t = 0; t < dg.back().enc_tiles; ++t) items.push_back({RI_ENC, gi, t});
     }
+    // a long code's spectrum item precedes the digit items that read it
+    for (int gi = 0; gi < (int)pers.size(); ++gi)
+      if (dg[gi].has_plan && dg[gi].long_plan) items.push_back({RI_SPEC, gi, 0});
     for (int gi = 0; gi < (int)pers.size(); ++gi)
       if (dg[gi].has_plan)
         for (int t = 0; t < dg[gi].plan.D; ++t) items.push_back({RI_PLAN, gi, t});
@@ -293,7 +393,7 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
       for (int t = 0; t < tiles; ++t) items.push_back({RI_DEC, gi, t});
     }
     const size_t G = dg.size();
-    r->counter_bytes = (1 + 2 * G) * sizeof(unsigned);
+    r->counter_bytes = (1 + 3 * G) * sizeof(unsigned);
     if (cudaMalloc(&r->d_groups, G * sizeof(RaggedGroupDev)) != cudaSuccess ||
         cudaMalloc(&r->d_items, items.size() * sizeof(RaggedItem)) != cudaSuccess ||
         cudaMalloc(&r->d_counters, r->counter_bytes) != cudaSuccess ||
@@ -308,10 +408,22 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     r->ra.next = r->d_counters;
     r->ra.enc_done = r->d_counters + 1;
     r->ra.plan_done = r->d_counters + 1 + G;
+    r->ra.spec_done = r->d_counters + 1 + 2 * G;
     r->npersistent = (int)G;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->dev);
     r->grid = std::max(1, sms);
+    // split-transform scratch: one area per persistent CTA, as large as the
+    // largest split item of the batch needs
+    size_t cta_words = 0;
+    for (int i : pers) cta_words = std::max(cta_words, cta_scratch_words(r->groups[i]));
+    if (cta_words) {
+      cta_words = (cta_words + 63) / 64 * 64;
+      if (cudaMalloc(&r->cta_scratch, (size_t)r->grid * cta_words * 4) != cudaSuccess)
+        return fail(FNT_RS_E_CUDA);
+    }
+    r->ra.cta_scratch = r->cta_scratch;
+    r->ra.cta_words = cta_words;
   }
   // schedules of the per-group launches: tune each such plan on its widest group
   {
@@ -354,10 +466,12 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
   }
   r->streams.resize(S);
   r->ws.assign(S, nullptr);
+  // Workspace per stream: for the per-group launches of the graph, and for
+  // fnt_rs_ragged_run_plain, which runs every group (persistent ones too, on
+  // stream 0's workspace) one after another through the plain calls.
   std::vector<size_t> wsb(S, 0);
   for (auto& rg : r->groups) {
-    if (rg.persistent) continue;
-    rg.stream = assign[rg.plan];
+    rg.stream = rg.persistent ? 0 : assign[rg.plan];
     fnt_rs_plan_s* p = rg.plan;
     // every schedule the plan may run (the tuner may have picked the direct product)
     size_t need = std::max(ws_bytes(p, rg.g.W, enc_nbuf_max(p)), direct_ws_bytes(p, rg.g.W));

@@ -1,9 +1,11 @@
 // The ragged persistent kernel: one launch runs the encode tiles, pattern
-// builds and decode tiles of every group with 256 <= n <= 8192 in a
-// ragged batch.  CTAs stay resident and take work items in list order from an
-// atomic counter; the list puts all encode and pattern items before the
-// decode items, so a decode item only ever waits (boundedly) on items that
-// running CTAs already hold, and the wait always ends.
+// builds and decode tiles of every group with n >= 256 in a ragged batch.
+// CTAs stay resident and take work items in list order from an atomic
+// counter; the list puts all encode, spectrum and pattern items before the
+// decode items (and every spectrum item before the digit items that read
+// it), so an item only ever waits (boundedly) on items that running CTAs
+// already hold, and every wait ends.  Data written by other CTAs of the same
+// launch (encoded rows, pattern tables, spectra) is read through L2 only.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +20,9 @@ namespace {
 template <int L>
 using RS = typename SchedFor<L>::type;
 constexpr int NT = kRaggedNT;
+using SLoc = SchedFor<kLocalL>::type;
+constexpr int WL = kRaggedSplitWT;
+static_assert(WL == wt_one(kLocalL), "a split item is one local tile wide");
 
 template <int L>
 __device__ __noinline__ void rg_encode(const KArgs& a, int tx) {
@@ -73,6 +78,250 @@ __device__ __noinline__ void rg_plan_tail(const RaggedGroupDev& g) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split transforms run by one CTA over the columns of one work item (x.W <=
+// WL): the radix-C cross pass into the CTA's scratch x.out2, then the C local
+// 4096-point passes, each a tile transform whose output goes where x.mode
+// says (kargs.h).  The same arithmetic as the standalone cross and local
+// kernels; the global scratch is written and read by this CTA only, between
+// CTA barriers.
+// ---------------------------------------------------------------------------
+// U (i2, column) pairs per thread at a time: the loads of the U groups are
+// independent, so a thread keeps U * C loads in flight (one CTA per SM has to
+// cover the memory latency of the whole pass by itself).
+template <int C, bool INV, int LOADM>
+__device__ __noinline__ void cta_cross(const KArgs& x) {
+  constexpr int U = C <= 8 ? 4 : 2;
+  uint32_t bad = 0u;
+  const int total = x.L * x.W;
+  int t = threadIdx.x;
+  for (; t + (U - 1) * NT < total; t += U * NT) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int tu = t + u * NT;
+      cross_one<C, INV, LOADM, true>(x, tu / x.W, tu % x.W, bad);
+    }
+  }
+  for (; t < total; t += NT) cross_one<C, INV, LOADM, true>(x, t / x.W, t % x.W, bad);
+  if (bad) atomicOr(x.status, ST_RANGE);
+}
+
+__device__ void cross_rt(const KArgs& x, bool inv, int lm) {
+  if (x.C == 16) {
+    if (!inv && lm == CL_SRC16) cta_cross<16, false, CL_SRC16>(x);
+    else if (inv && lm == CL_RECV) cta_cross<16, true, CL_RECV>(x);
+    else if (inv) cta_cross<16, true, CL_U32>(x);
+    else cta_cross<16, false, CL_U32>(x);
+  } else {  // C = 8
+    if (!inv && lm == CL_SRC16) cta_cross<8, false, CL_SRC16>(x);
+    else if (inv && lm == CL_RECV) cta_cross<8, true, CL_RECV>(x);
+    else if (inv) cta_cross<8, true, CL_U32>(x);
+    else cta_cross<8, false, CL_U32>(x);
+  }
+  __syncthreads();
+}
+
+template <bool INV>
+__device__ __noinline__ void cta_local(const KArgs& x) {
+  for (int j1 = 0; j1 < x.C; ++j1) {
+    tile_body<SLoc, WL, NT, INV, LoadRows32<WL>, StoreLocalRT<WL, true>>(x, 0, j1);
+    __syncthreads();
+  }
+}
+
+__device__ void local_rt(const KArgs& x, bool inv) {
+  if (inv) cta_local<true>(x);
+  else cta_local<false>(x);
+}
+
+// Encode of columns [tile*WL, +WL) of a long code (Sec. II.B: e = FNT of the
+// zero-padded source), split as n = C * 4096.
+__device__ void split_encode(const RaggedGroupDev& g, int tile, uint32_t* scr) {
+  KArgs c = g.xenc;
+  const int c0 = tile * WL;
+  c.W = min(WL, g.enc.W - c0);
+  c.in = static_cast<const uint16_t*>(g.enc.in) + c0;
+  c.ld_in = g.enc.ld_in;
+  c.out = static_cast<uint32_t*>(g.enc.out) + c0;
+  c.ld_out = g.enc.ld_out;
+  c.out2 = scr;
+  c.ld_work = (size_t)c.W;
+  c.row_limit = g.enc.k;
+  cross_rt(c, false, CL_SRC16);
+  KArgs x = c;
+  x.in = scr;
+  x.ld_in = (size_t)c.W;
+  x.mode = LM_ENC;
+  local_rt(x, false);
+}
+
+// Decode (steps 4-6 of Sec. II.B) of columns [tile*WL, +WL) of a long code,
+// the same pass sequence as the standalone split decode: k <= n/2 in 6
+// passes, k > n/2 (product split at h = n/2) in 10.
+__device__ void split_decode(const RaggedGroupDev& g, int tile, uint32_t* scr) {
+  const int n = g.L, k = g.dec.k, h = n / 2;
+  const int c0 = tile * WL;
+  const int w = min(WL, g.dec.W - c0);
+  KArgs c = g.xdec;
+  c.W = w;
+  c.ld_work = (size_t)w;
+  c.out = static_cast<uint16_t*>(g.dec.out) + c0;
+  c.ld_out = g.dec.ld_out;
+  const uint32_t* recv = static_cast<const uint32_t*>(g.dec.in) + c0;
+  const size_t nw = (size_t)n * w;
+  uint32_t* A = scr;
+  uint32_t* B0 = A + nw;
+  uint32_t* B1 = B0 + nw;
+  uint32_t* B2 = B1 + nw;
+  auto cross = [&](bool inv, int lm, const void* in, size_t ld_in, int row_limit) {
+    KArgs x = c;
+    x.in = in;
+    x.ld_in = ld_in;
+    x.row_limit = row_limit;
+    x.out2 = A;
+    cross_rt(x, inv, lm);
+  };
+  auto local = [&](bool inv, int mode, void* o2, void* o3, int out_limit, const void* in2) {
+    KArgs x = c;
+    x.in = A;
+    x.ld_in = (size_t)w;
+    x.out2 = o2;
+    x.out3 = o3;
+    x.in2 = in2;
+    x.out_limit = out_limit;
+    x.mode = mode;
+    local_rt(x, inv);
+  };
+  if (!g.blocked) {
+    cross(true, CL_RECV, recv, g.dec.ld_in, n);
+    local(true, LM_WORK, B0, nullptr, k, nullptr);
+    cross(false, CL_U32, B0, (size_t)w, k);
+    local(false, LM_WORK_AHAT, B0, nullptr, n, nullptr);
+    cross(true, CL_U32, B0, (size_t)w, n);
+    local(true, LM_OUT16, nullptr, nullptr, k, nullptr);
+  } else {
+    cross(true, CL_RECV, recv, g.dec.ld_in, n);
+    local(true, LM_SPLIT, B0, B1, k, nullptr);
+    cross(false, CL_U32, B0, (size_t)w, h);
+    local(false, LM_X_PARTIAL, B0, B2, n, nullptr);
+    cross(false, CL_U32, B1, (size_t)w, k - h);
+    local(false, LM_ACCUM, nullptr, B2, n, nullptr);
+    cross(true, CL_U32, B2, (size_t)w, n);
+    local(true, LM_WORK, B1, nullptr, n, nullptr);
+    cross(true, CL_U32, B0, (size_t)w, n);
+    local(true, LM_OUT16_ADD, nullptr, nullptr, k, B1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pattern build of a long code (n >= 32768), the log-domain route of the
+// one-launch build with its transforms over global scratch: one transform of
+// a column (or two) of length L, as a one-CTA tile (L <= 32768) or split
+// (L = 65536).  base = the group's colf / coli (tables, n, L, C).
+// ---------------------------------------------------------------------------
+template <int L, bool INV>
+__device__ __noinline__ void col_fnt(const KArgs& base, const uint32_t* in, size_t ld_in,
+                                     uint32_t* out, size_t ld_out, int W, uint32_t scale,
+                                     uint32_t* scr) {
+  KArgs x = base;
+  x.in = in;
+  x.ld_in = ld_in;
+  x.out = out;
+  x.ld_out = ld_out;
+  x.W = W;
+  x.scale = scale;
+  if constexpr (L <= kTileMaxL) {
+    constexpr int WT = wt_one(L);
+    for (int tx = 0; tx * WT < W; ++tx) {
+      tile_body<RS<L>, WT, NT, INV, LoadRows32<WT>, StoreRows32<WT>>(x, tx, 0);
+      __syncthreads();
+    }
+  } else {
+    x.row_limit = L;
+    x.out2 = scr;
+    x.ld_work = (size_t)W;
+    cross_rt(x, INV, CL_U32);
+    KArgs y = x;
+    y.in = scr;
+    y.ld_in = (size_t)W;
+    y.mode = LM_FNT;
+    local_rt(y, INV);
+  }
+}
+
+// The spectrum item: position table rows, then spec = FNT(1_R).
+template <int L>
+__device__ __noinline__ void rg_spec(const RaggedGroupDev& g, unsigned* done, uint32_t* scr) {
+  const LongPlanDev& lp = g.lp;
+  const int k = g.dec.k;
+  for (int z = threadIdx.x; z < L; z += NT) lp.ind[z] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += NT) lp.ind[__ldg(g.plan.pos + i)] = (uint32_t)i + 1u;
+  __syncthreads();
+  for (int z = threadIdx.x; z < L; z += NT) {
+    const uint32_t r = lp.ind[z];
+    g.plan.pat[z] = make_uint2(r ? r - 1u : 0xFFFFFFFFu, 0u);
+    lp.ind[z] = r ? 1u : 0u;
+  }
+  __syncthreads();
+  col_fnt<L, false>(g.colf, lp.ind, 1, lp.spec, 1, 1, 1u, scr);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(done, 1u);
+}
+
+// Digit t: conv[.][t] = n^-1 IFNT(spec * ghat[.][t]).  The last digit item of
+// the group recombines the digits into the tables (and, for k > n/2, the
+// transforms of the two halves of A mod x^k); returns true in that CTA.
+template <int L>
+__device__ __noinline__ bool rg_digit(const RaggedGroupDev& g, int t, uint32_t* scr) {
+  __shared__ int s_last;
+  const LongPlanDev& lp = g.lp;
+  const PlanArgs& pa = g.plan;
+  uint32_t* pr = lp.prod + (size_t)t * L;
+  for (int j = threadIdx.x; j < L; j += NT)
+    pr[j] = m_mul(__ldg(pa.ghat + (size_t)j * pa.D + t), __ldcg(lp.spec + j));
+  __syncthreads();
+  col_fnt<L, true>(g.coli, pr, 1, pa.conv + t, (size_t)pa.D, 1, pa.ninv, scr);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(pa.done, 1u) == (uint32_t)pa.D - 1u;
+  __syncthreads();
+  const bool last = s_last;
+  __syncthreads();  // s_last is rewritten by the next digit this CTA runs
+  if (!last) return false;
+  __threadfence();
+  const int k = g.dec.k;
+  const LogFinal f{pa.conv, pa.D, pa.b, L, k, pa.exp3, pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat};
+  lg_final_block<L, NT>(f);
+  if (g.blocked) {
+    __syncthreads();
+    constexpr int H = L / 2;
+    col_fnt<L, true>(g.coli, lp.aval, 1, lp.coef, 1, 1, pa.ninv, scr);
+    for (int j = threadIdx.x; j < L; j += NT) {
+      uint32_t a0 = 0u, a1 = 0u;
+      if (k == L) {
+        a0 = j == 0 ? kP - 1u : 0u;  // A = x^n - 1, A mod x^n = -1
+      } else {
+        if (j < H) a0 = lp.coef[j];
+        if (j < k - H) a1 = lp.coef[H + j];
+      }
+      lp.M2[2 * j] = a0;
+      lp.M2[2 * j + 1] = a1;
+    }
+    __syncthreads();
+    col_fnt<L, false>(g.colf, lp.M2, 2, lp.E2, 2, 2, 1u, scr);
+    uint32_t* ahat = const_cast<uint32_t*>(g.dec.ahat);
+    uint32_t* ahat2 = const_cast<uint32_t*>(g.dec.ahat2);
+    for (int j = threadIdx.x; j < L; j += NT) {
+      ahat[j] = p_mul(lp.E2[2 * j], pa.ninv);
+      ahat2[j] = p_mul(lp.E2[2 * j + 1], pa.ninv);
+    }
+  }
+  if (threadIdx.x == 0) *pa.done = 0u;
+  return true;
+}
+
 // Bounded wait until *p >= target; false if the bound ran out.
 __device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target) {
   for (uint32_t i = 0; i < kWaitPolls; ++i) {
@@ -84,6 +333,7 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target
   return false;
 }
 
+// tile bodies: every length up to 32768 (pattern builds in one launch up to 16384)
 #define FNTRS_RAGGED_SWITCH(L, CALL) \
   switch (L) {                       \
     case 256: CALL(256); break;      \
@@ -92,11 +342,31 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target
     case 2048: CALL(2048); break;    \
     case 4096: CALL(4096); break;    \
     case 8192: CALL(8192); break;    \
+    case 16384: CALL(16384); break;  \
+    case 32768: CALL(32768); break;  \
     default: break;                  \
+  }
+#define FNTRS_RAGGED_SWITCH_FUSED(L, CALL) \
+  switch (L) {                             \
+    case 256: CALL(256); break;            \
+    case 512: CALL(512); break;            \
+    case 1024: CALL(1024); break;          \
+    case 2048: CALL(2048); break;          \
+    case 4096: CALL(4096); break;          \
+    case 8192: CALL(8192); break;          \
+    case 16384: CALL(16384); break;        \
+    default: break;                        \
+  }
+#define FNTRS_RAGGED_SWITCH_LONG(L, CALL) \
+  switch (L) {                            \
+    case 32768: CALL(32768); break;       \
+    case 65536: CALL(65536); break;       \
+    default: break;                       \
   }
 
 __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
   __shared__ int s_item, s_ok;
+  uint32_t* scr = ra.cta_scratch ? ra.cta_scratch + (size_t)blockIdx.x * ra.cta_words : nullptr;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(ra.next, 1u);
     __syncthreads();
@@ -107,24 +377,47 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
     const RaggedGroupDev& g = ra.groups[item.group];
     const int L = g.L;
     if (item.kind == RI_ENC) {
+      if (g.split_enc) {
+        split_encode(g, item.tile, scr);
+      } else {
 #define FNTRS_CALL(X) rg_encode<X>(g.enc, item.tile)
-      FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
+        FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
 #undef FNTRS_CALL
+      }
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) atomicAdd(ra.enc_done + item.group, 1u);
+    } else if (item.kind == RI_SPEC) {
+#define FNTRS_CALL(X) rg_spec<X>(g, ra.spec_done + item.group, scr)
+      FNTRS_RAGGED_SWITCH_LONG(L, FNTRS_CALL)
+#undef FNTRS_CALL
     } else if (item.kind == RI_PLAN) {
       bool last = false;
-#define FNTRS_CALL(X) last = rg_plan<X>(g.plan, item.tile)
-      FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
-#undef FNTRS_CALL
-      if (last) {
-        if (g.blocked) {
-          __syncthreads();
-#define FNTRS_CALL(X) rg_plan_tail<X>(g)
-          FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
+      if (g.long_plan) {
+        if (threadIdx.x == 0) {
+          const bool ok = wait_at_least(ra.spec_done + item.group, 1u);
+          if (!ok) atomicOr(g.dec.status, ST_TIMEOUT);
+          __threadfence();
+          s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+#define FNTRS_CALL(X) last = rg_digit<X>(g, item.tile, scr)
+          FNTRS_RAGGED_SWITCH_LONG(L, FNTRS_CALL)
 #undef FNTRS_CALL
         }
+      } else {
+#define FNTRS_CALL(X) last = rg_plan<X>(g.plan, item.tile)
+        FNTRS_RAGGED_SWITCH_FUSED(L, FNTRS_CALL)
+#undef FNTRS_CALL
+        if (last && g.blocked) {
+          __syncthreads();
+#define FNTRS_CALL(X) rg_plan_tail<X>(g)
+          FNTRS_RAGGED_SWITCH_FUSED(L, FNTRS_CALL)
+#undef FNTRS_CALL
+        }
+      }
+      if (last) {
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicExch(ra.plan_done + item.group, 1u);
@@ -139,9 +432,11 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
       }
       __syncthreads();
       if (s_ok) {
-        if (g.blocked) {
+        if (g.split_dec) {
+          split_decode(g, item.tile, scr);
+        } else if (g.blocked) {
 #define FNTRS_CALL(X) rg_decode_split<X>(g.dec, item.tile)
-          FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
+          FNTRS_RAGGED_SWITCH_FUSED(L, FNTRS_CALL)
 #undef FNTRS_CALL
         } else {
 #define FNTRS_CALL(X) rg_decode<X>(g.dec, item.tile)
@@ -158,8 +453,8 @@ template <int L>
 constexpr int body_smem_words() {
   using S = RS<L>;
   const int one = smem_words<S, wt_one(L)>();
-  const int two = 2 * smem_words<S, wt_two(L)>();
-  const int plan = Lay<S, 1>::WORDS + L;
+  const int two = L <= 16384 ? 2 * smem_words<S, wt_two(L)>() : 0;
+  const int plan = L <= 16384 ? Lay<S, 1>::WORDS + L : 0;
   return std::max(one, std::max(two, plan));
 }
 
@@ -168,7 +463,8 @@ constexpr int body_smem_words() {
 int ragged_smem_bytes() {
   const int w = std::max({body_smem_words<256>(), body_smem_words<512>(), body_smem_words<1024>(),
                           body_smem_words<2048>(), body_smem_words<4096>(),
-                          body_smem_words<8192>()});
+                          body_smem_words<8192>(), body_smem_words<16384>(),
+                          body_smem_words<32768>(), smem_words<SLoc, WL>()});
   return w * 4;
 }
 
@@ -180,11 +476,15 @@ int ragged_wt_enc(int L) {
     case 2048: return wt_one(2048);
     case 4096: return wt_one(4096);
     case 8192: return wt_one(8192);
+    case 16384: return wt_one(16384);
+    case 32768: return wt_one(32768);
+    case 65536: return kRaggedSplitWT;
     default: return 0;
   }
 }
 
 int ragged_wt_dec(int L, bool blocked) {
+  if (ragged_split_dec(L, blocked)) return kRaggedSplitWT;
   if (!blocked) return ragged_wt_enc(L);
   switch (L) {
     case 256: return wt_two(256);
@@ -193,6 +493,7 @@ int ragged_wt_dec(int L, bool blocked) {
     case 2048: return wt_two(2048);
     case 4096: return wt_two(4096);
     case 8192: return wt_two(8192);
+    case 16384: return wt_two(16384);
     default: return 0;
   }
 }

@@ -48,7 +48,9 @@ def test_ragged_graph_round_trip_and_oracle(pkg):
     try:
         info = pkg.fnt_rs_ragged_info(r)
         assert info["groups"] == 36
-        assert 0 < info["persistent_groups"] < 36  # tile-sized codes in the persistent kernel
+        # every code with n >= 256 runs in the persistent kernel, shorter ones per group
+        assert info["persistent_groups"] == sum(g["n"] >= 256 for g in groups)
+        assert 0 < info["persistent_groups"] < 36
         for g in groups:  # creation already ran the batch once; clear and rerun by graph
             g["enc"].zero_()
             g["out"].zero_()
@@ -135,5 +137,65 @@ def test_ragged_persistent_kernel_groups(pkg):
         for i, g in enumerate(groups):
             assert np.array_equal(pkg.to_host(g["enc"]), first[i][0])
             assert np.array_equal(pkg.to_host(g["out"]), first[i][1])
+    finally:
+        pkg.fnt_rs_ragged_destroy(r)
+
+
+def test_ragged_long_codes_in_one_persistent_launch(pkg):
+    # every long length at every rate of the ragged batch: one-CTA tiles for
+    # n = 16384 and for n = 32768 at rate 1/2, split transforms run inside one
+    # CTA per 8-column item for n = 65536 and for n = 32768 above rate 1/2, and
+    # the long pattern builds (spectrum item + digit items) for n >= 32768;
+    # widths that are not multiples of the item width, some encode-only groups,
+    # and a few short codes in the same launch
+    shapes = [(16384, 8192, 9), (16384, 12288, 5), (16384, 14336, 4), (32768, 16384, 3),
+              (32768, 21845, 11), (32768, 28672, 8), (65536, 32768, 13), (65536, 43690, 6),
+              (65536, 49152, 17), (65536, 57344, 4), (4096, 3072, 20), (256, 128, 40),
+              (65536, 32768, 10), (32768, 24576, 9)]
+    groups = []
+    for i, (n, k, W) in enumerate(shapes):
+        src = synth.source(700 + i, k, W)
+        pos = synth.received_positions(n, synth.erased_uniform(800 + i, n, k))
+        groups.append({"n": n, "k": k, "src_h": src, "src": pkg.to_device(src),
+                       "enc": torch.zeros((n, W), dtype=torch.int32, device="cuda"),
+                       "out": torch.zeros((k, W), dtype=torch.int16, device="cuda"),
+                       "positions": pos if i not in (3, 12) else None})
+    r = pkg.fnt_rs_ragged_create(groups, nstreams=2)
+    try:
+        info = pkg.fnt_rs_ragged_info(r)
+        assert info["persistent_groups"] == len(groups)
+        rng = np.random.default_rng(13)
+        first = None
+        for rep in range(2):
+            for g in groups:
+                g["enc"].zero_()
+                g["out"].zero_()
+            pkg.fnt_rs_ragged_run(r)
+            torch.cuda.synchronize()
+            assert pkg.fnt_rs_ragged_status(r) == 0
+            got = [(pkg.to_host(g["enc"]), pkg.to_host(g["out"])) for g in groups]
+            if first is None:
+                first = got
+            for i, g in enumerate(groups):
+                assert np.array_equal(got[i][0], first[i][0]), shapes[i]
+                assert np.array_equal(got[i][1], first[i][1]), shapes[i]
+                if g["positions"] is not None:
+                    assert np.array_equal(got[i][1], g["src_h"]), shapes[i]
+        for i, g in enumerate(groups):  # encoded rows by Horner (O(k) each)
+            n, k = g["n"], g["k"]
+            W = g["src_h"].shape[1]
+            cols = [0, W - 1]
+            rows = np.sort(rng.choice(n, 3, replace=False)).astype(np.uint32)
+            want = oracle.encode_rows(np.ascontiguousarray(g["src_h"][:, cols]), n, rows)
+            assert np.array_equal(first[i][0][rows][:, cols], want), shapes[i]
+        # per-group plain launches give the same bits
+        for g in groups:
+            g["enc"].zero_()
+            g["out"].zero_()
+        pkg.fnt_rs_ragged_run_plain(r)
+        torch.cuda.synchronize()
+        for i, g in enumerate(groups):
+            assert np.array_equal(pkg.to_host(g["enc"]), first[i][0]), shapes[i]
+            assert np.array_equal(pkg.to_host(g["out"]), first[i][1]), shapes[i]
     finally:
         pkg.fnt_rs_ragged_destroy(r)
