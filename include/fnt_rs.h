@@ -67,7 +67,8 @@ enum fnt_rs_status_code {
   FNT_RS_E_CUDA = -6,           /* a CUDA runtime call failed */
   FNT_RS_E_RANGE = -7,          /* status: decoded 65536 (written as 0) or received > 65536 */
   FNT_RS_E_TIMEOUT = -8,        /* status: a bounded device wait gave up */
-  FNT_RS_E_WORKSPACE = -9       /* workspace missing or too small */
+  FNT_RS_E_WORKSPACE = -9,      /* workspace missing or too small */
+  FNT_RS_E_BOUNDS = -10         /* status, debug build only: a device index check failed */
 };
 
 enum fnt_rs_op {
@@ -412,9 +413,20 @@ int fnt_rs_decode_wire_host(fnt_rs_plan plan, const uint16_t* h_recv, const uint
 
 /*
  * Reads the plan's device status word (synchronising `stream`), clears it and
- * returns FNT_RS_OK, FNT_RS_E_RANGE or FNT_RS_E_TIMEOUT (the most severe seen).
+ * returns FNT_RS_OK, FNT_RS_E_RANGE, FNT_RS_E_BOUNDS (debug build) or
+ * FNT_RS_E_TIMEOUT (the most severe seen).
  */
 int fnt_rs_status(fnt_rs_plan plan, void* stream);
+
+/*
+ * 1 if this library is the debug build (not part of the paper's method; a
+ * development aid): every shared-memory index of the transform passes and
+ * every global index of the loaders, storers and staged tiles is checked on
+ * the device, and a failed check skips the access and raises FNT_RS_E_BOUNDS
+ * in the status word instead of faulting.  0 in the release build, where the
+ * checks are compiled out.
+ */
+int fnt_rs_debug_bounds(void);
 
 /*
  * Ragged batches (many codeword groups of different n, k, W and erasure

@@ -32,6 +32,7 @@ SCHED_NAMES = {SCHED_TMA: "tma", SCHED_TILE: "tile", SCHED_SPLIT: "split", SCHED
 
 E_RANGE = -7
 E_TIMEOUT = -8
+E_BOUNDS = -10
 
 
 def _stream(stream) -> int:
@@ -419,6 +420,11 @@ def fnt_rs_autotune(plan, W: int, op: int, stream=None) -> list:
 
 def fnt_rs_status(plan, stream=None) -> int:
     return int(load().fnt_rs_status(plan, _stream(stream)))
+
+
+def fnt_rs_debug_bounds() -> int:
+    """1 if the loaded library is the debug build with device index checks."""
+    return int(load().fnt_rs_debug_bounds())
 
 
 def fnt_rs_strerror(code: int) -> str:

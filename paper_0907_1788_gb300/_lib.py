@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libfntrs.so")
+# FNTRS_LIB selects another in-tree build of the same library (the debug
+# build with device index checks); by default the release build is loaded.
+LIB_PATH = os.environ.get("FNTRS_LIB") or os.path.join(HERE, "_build", "libfntrs.so")
 
 _lock = threading.Lock()
 _lib = None
@@ -55,6 +57,7 @@ def load(build_if_missing: bool = False):
             "fnt_rs_fnt": (i32, [vp, vp, sz, vp, sz, sz, i32, vp, vp]),
             "fnt_rs_encode_host": (i32, [vp, vp, vp, sz, vp, vp]),
             "fnt_rs_encode_noalloc": (i32, [vp, vp, sz, vp, sz, sz, vp]),
+            "fnt_rs_debug_bounds": (i32, []),
             "fnt_rs_decode_host": (i32, [vp, vp, vp, u32, vp, sz, vp, vp]),
             "fnt_rs_plan_set_length": (i32, [vp, u32]),
             "fnt_rs_encode_sys": (i32, [vp, vp, sz, vp, sz, sz, vp, vp]),

@@ -19,6 +19,7 @@ template <class S, int NT>
 __global__ void __launch_bounds__(NT, 1)
     k_encode_tma_fold(KArgs a, const uint32_t* __restrict__ twc, int rows_staged, int box_rows,
                       const __grid_constant__ CUtensorMap tsrc) {
+  dbg_enter(a.status);
   static_assert(S::NP == 3 || S::NP == 2, "");
   static_assert(2 * S::R1 <= 32, "class-1 pass-1 factors must be rotations");
   constexpr int WS = 8, WT = 4, C = 2;  // staged / transformed codewords per tile

@@ -6,8 +6,9 @@
 
 namespace fntrs {
 
-// Status bits ORed into the plan's device status word.
-enum : int { ST_RANGE = 1, ST_TIMEOUT = 2 };
+// Status bits ORed into the plan's device status word (ST_BOUNDS: a device
+// index check of the debug build failed, dbg.cuh).
+enum : int { ST_RANGE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
 
 // Output modes of the local (in-tile) pass of a split transform n = C * L.
 enum LocalMode : int {
@@ -88,6 +89,7 @@ struct PlanArgs {
   uint32_t* aval = nullptr;        // A(r^j) (split step-6 product) or null
   uint32_t* ahat = nullptr;        // n^-1 FNT(A mod x^k) or null
   uint32_t* done = nullptr;        // CTA completion counter, zero between builds
+  int* status = nullptr;           // the plan's status word (debug-build index checks)
 };
 
 }  // namespace fntrs

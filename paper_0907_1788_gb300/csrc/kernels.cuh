@@ -48,6 +48,7 @@ struct LoadSrcFold {
     uint32_t acc = 0u;
     int row = i;
     for (int m = 0; m < C && row < k; ++m, row += L) {
+      if (!dbg_in(row, k)) break;
       const uint32_t v = src[(size_t)row * ld + col];
       acc = m == 0 ? v : m_add(acc, m_rot_rt(v, (uint32_t)(eC * m * cc)));
     }
@@ -73,6 +74,7 @@ struct LoadRows32 {
     if (col >= W) return 0u;
     size_t row = row0 + i;
     if (rmul != 1u) row = (rmul * (uint32_t)row) & nmask;
+    if (!dbg_in((long long)row, (long long)nmask + 1)) return 0u;
     return in[row * ld + col];
   }
 };
@@ -91,10 +93,11 @@ struct LoadRecv {
   int* status;
   int col0, W, slots;
   uint32_t bad;
+  int rows;  // rows of the received matrix: n (slots) or the first k positions (packed)
   static __device__ __forceinline__ LoadRecv make(const KArgs& a, int tx, int ty) {
     (void)ty;
     return LoadRecv{static_cast<const uint32_t*>(a.in), a.ld_in, a.pat, a.status, tx * WT, a.W,
-                    a.slots, 0u};
+                    a.slots, 0u, a.slots ? a.n : a.k};
   }
   __device__ __forceinline__ uint32_t operator()(int i, int c) {
     const int col = col0 + c;
@@ -102,6 +105,7 @@ struct LoadRecv {
     uint32_t v = 0u;
     if (e.y != 0u && col < W) {
       const size_t row = slots ? (size_t)i : (size_t)e.x;
+      if (!dbg_in((long long)row, rows, status)) return 0u;
       v = CG ? __ldcg(recv + row * ld + col) : recv[row * ld + col];
     }
     bad |= v > 65536u ? 1u : 0u;
@@ -162,6 +166,7 @@ struct StoreRows32 {
     if (scale != 1u) v = m_mul(v, scale);
     uint32_t row = (uint32_t)(cc + C * j);
     if (rmul != 1u) row = (rmul * row) & nmask;
+    if (!dbg_in(row, (long long)nmask + 1)) return;
     if (wire)
       wo.put(row, col, m_to_p(v));
     else
@@ -185,6 +190,7 @@ template <int MODE, bool CG = false>
 __device__ __forceinline__ void local_store(const KArgs& a, int j1, int j, int col, uint32_t v,
                                             uint32_t& bad) {
   const size_t row = (size_t)j1 + (size_t)a.C * j;
+  if (!dbg_in((long long)row, a.n, a.status)) return;
   if constexpr (MODE == LM_ENC || MODE == LM_FNT) {
     if (MODE == LM_FNT && a.scale != 1u) v = m_mul(v, a.scale);
     const size_t orow =
@@ -309,6 +315,7 @@ __device__ __forceinline__ void tile_body(const KArgs& a, int tx, int ty) {
 
 template <class S, int WT, int NT, bool INV, class LD, class ST>
 __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
+  dbg_enter(a.status);
   tile_body<S, WT, NT, INV, LD, ST>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -330,6 +337,7 @@ __global__ void __launch_bounds__(NT, 1)
                  const __grid_constant__ CUtensorMap tsrc) {
   static_assert(S::NP == 3 || S::NP == 2, "");
   static_assert(C == 1 || (C == 2 && 2 * S::R1 <= 32), "");
+  dbg_enter(a.status);
   using Y = Lay<S, WT>;
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
@@ -433,6 +441,9 @@ __global__ void __launch_bounds__(NT, 1)
         constexpr int RL = S::RL, BL = ilog2(RL);
         for (int t = threadIdx.x; t < (S::L / RL) * WT; t += NT) {
           const int c = t % WT, b = t / WT;
+          if (!dbg_in(cc + C * (S::natural(b * RL) + (RL - 1) * (S::L / RL)), C * S::L) ||
+              !dbg_in(b * Y::LAST_B + c + (RL - 1) * WT, Y::WORDS))
+            continue;
           const uint32_t* base = work + b * Y::LAST_B + c;
           uint32_t x[RL];
 #pragma unroll
@@ -489,6 +500,10 @@ __device__ __forceinline__ void cross_one(const KArgs& a, int i2, int col, uint3
 #pragma unroll
   for (int q = 0; q < C; ++q) {
     const int row = q * a.L + i2;
+    if (!dbg_in(row, a.n, a.status)) {
+      x[q] = 0u;
+      continue;
+    }
     if constexpr (LOADM == CL_SRC16) {
       x[q] = row < a.row_limit
                  ? (uint32_t) static_cast<const uint16_t*>(a.in)[(size_t)row * a.ld_in + col]
@@ -502,7 +517,7 @@ __device__ __forceinline__ void cross_one(const KArgs& a, int i2, int col, uint3
     } else {
       const uint2 e = ld_tab<CG>(a.pat + row);
       uint32_t v = 0u;
-      if (e.y != 0u) {
+      if (e.y != 0u && dbg_in(a.slots ? 0 : (long long)e.x, a.k, a.status)) {
         const size_t rr = a.slots ? (size_t)row : (size_t)e.x;
         const uint32_t* src = static_cast<const uint32_t*>(a.in) + rr * a.ld_in + col;
         v = CG ? __ldcg(src) : *src;
@@ -697,6 +712,7 @@ __device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
 
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
+  dbg_enter(a.status);
   decode_body<S, WT, NT>(a, blockIdx.x);
 }
 
@@ -714,9 +730,11 @@ struct LoadStaged {
   const uint32_t* stage;
   const uint32_t* pat32;
   uint32_t vmax;  // largest received value seen (> 65536 is out of range)
+  int rows = 1 << 17;  // staged rows (the debug build checks the row index)
   // unused positions have weight 0 and row 0: the product vanishes, no branch
   __device__ __forceinline__ uint32_t operator()(int z, int c) {
     const uint32_t e = __ldg(pat32 + z);
+    if (!dbg_in(e >> 17, rows)) return 0u;
     const uint32_t v = stage[(e >> 17) * WT + c];
     vmax = max(vmax, v);
     return m_mul(v, e & 0x1FFFFu);
@@ -820,6 +838,7 @@ __global__ void __launch_bounds__(NT, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
                  int nfull, const __grid_constant__ CUtensorMap trecv) {
   static_assert(S::NP >= 2, "");
+  dbg_enter(a.status);
   using Y = Lay<S, WT>;
   constexpr int WH = WT >= 2 ? WT / 2 : 1;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
@@ -851,7 +870,7 @@ __global__ void __launch_bounds__(NT, 1)
   }
   uint32_t parity = 0, cphase = 0;
   bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
-  LoadStaged<WT> load{stage, pat32, 0u};
+  LoadStaged<WT> load{stage, pat32, 0u, rows_staged};
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
   auto freed = [&]() {
@@ -889,7 +908,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (tile >= nfull) {
         // a half tile: columns (tile - nfull) & 1 of its box, WH codewords
         const int h = tile - nfull;
-        LoadStaged<WT> lh{stage + (h & 1) * WH, pat32, load.vmax};
+        LoadStaged<WT> lh{stage + (h & 1) * WH, pat32, load.vmax, rows_staged};
         store_h.col0 = nfull * WT + h * WH;
         decode_staged_tile<S, WH, NT, HALF>(sm, lh, store_h, a, freed);
         load.vmax = lh.vmax;
@@ -920,6 +939,7 @@ __global__ void __launch_bounds__(NT, 1)
 template <class S, int WT, int NT, bool HALF, int MINB = 2>
 __global__ void __launch_bounds__(NT, MINB)
     k_decode_cpa(KArgs a, const uint32_t* __restrict__ pat32) {
+  dbg_enter(a.status);
   static_assert(S::NP >= 2 && (WT == 1 || WT == 2 || WT == 4), "");
   using Y = Lay<S, WT>;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
@@ -948,7 +968,7 @@ __global__ void __launch_bounds__(NT, MINB)
     if (threadIdx.x == 0) clc_request(resp, cbar);
   }
   uint32_t cphase = 0;
-  LoadStaged<WT> load{stage, pat32, 0u};
+  LoadStaged<WT> load{stage, pat32, 0u, k};
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   while (tile < ntiles) {
     cp_async_wait_all();
@@ -1174,6 +1194,7 @@ __device__ __forceinline__ void decode_split_body(const KArgs& a, int tx) {
 
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT) k_decode_split(KArgs a) {
+  dbg_enter(a.status);
   decode_split_body<S, WT, NT>(a, blockIdx.x);
 }
 
@@ -1276,6 +1297,7 @@ __device__ __forceinline__ bool plan_body(const PlanArgs& pa, int t) {
 
 template <class S, int NT>
 __global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
+  dbg_enter(pa.status);
   plan_body<S, NT>(pa, blockIdx.x);
 }
 
@@ -1289,6 +1311,7 @@ __global__ void __launch_bounds__(NT) k_plan_fused(PlanArgs pa) {
 // ---------------------------------------------------------------------------
 template <class S, int WT, int NT>
 __global__ void __launch_bounds__(NT) k_poly_level(KArgs a) {
+  dbg_enter(a.status);
   static_assert(S::NP >= 2, "");
   using Y = Lay<S, WT>;
   extern __shared__ uint4 smem_raw[];

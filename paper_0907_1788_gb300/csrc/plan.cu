@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/fnt_rs.h"
+#include "dbg.cuh"
 #include "internal.h"
 #include "kargs.h"
 #include "sched.h"
@@ -470,6 +471,7 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32
     pa.aval = p->blocked ? aval : nullptr;
     pa.ahat = p->blocked ? nullptr : sl.ahat;
     pa.done = sl.done;
+    pa.status = p->status;
     ops.plan_fused(pa, st);
     if (!p->blocked) return cuda_ok(cudaGetLastError());
   } else {
@@ -947,6 +949,8 @@ const char* fnt_rs_strerror(int code) {
     case FNT_RS_E_CUDA: return "CUDA runtime error";
     case FNT_RS_E_RANGE: return "value out of range (decoded 65536 or received > 65536)";
     case FNT_RS_E_TIMEOUT: return "a bounded device wait gave up";
+    case FNT_RS_E_BOUNDS:
+      return "a device index check of the debug build failed (the access was skipped)";
     case FNT_RS_E_WORKSPACE:
       return "workspace missing or too small (or, for fnt_rs_encode_noalloc, the encode "
              "workspace exceeds FNT_RS_NOALLOC_SCRATCH_BYTES)";
@@ -1395,9 +1399,12 @@ int fnt_rs_status(fnt_rs_plan p, void* stream) {
   if (cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) return FNT_RS_E_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return FNT_RS_E_CUDA;
   if (h & ST_TIMEOUT) return FNT_RS_E_TIMEOUT;
+  if (h & ST_BOUNDS) return FNT_RS_E_BOUNDS;
   if (h & ST_RANGE) return FNT_RS_E_RANGE;
   return FNT_RS_OK;
 }
+
+int fnt_rs_debug_bounds(void) { return FNTRS_DEBUG_BOUNDS ? 1 : 0; }
 
 int fnt_rs_plan_info(fnt_rs_plan p, int* info, int cap) {
   if (!p || !info) return 0;

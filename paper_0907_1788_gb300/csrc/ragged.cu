@@ -141,6 +141,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   e.twi = p->tn.twi;
   e.powf = p->tn.powf;
   e.row_mul = p->uinv;
+  e.status = p->status;
   if (d.split_enc) {
     KArgs& x = d.xenc;  // the split encode's cross and local passes
     x.n = n;
@@ -225,6 +226,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
     pa.aval = p->blocked ? lp.aval : nullptr;
     pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
     pa.done = rg.tab.done;
+    pa.status = p->status;
     return d;
   }
   // scratch: conv [n][D] | aval [n] | coef [n] | halves [n][2] | E [n][2]
@@ -249,6 +251,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   pa.aval = p->blocked ? aval : nullptr;
   pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
   pa.done = rg.tab.done;
+  pa.status = p->status;
   d.halves = halves;
   KArgs& ti = d.tail_inv;
   ti.in = aval;

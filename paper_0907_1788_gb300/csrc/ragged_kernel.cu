@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
     const RaggedItem item = ra.items[it];
     const RaggedGroupDev& g = ra.groups[item.group];
     const int L = g.L;
+    dbg_enter(g.enc.status ? g.enc.status : g.dec.status);
     if (item.kind == RI_ENC) {
       if (g.split_enc) {
         split_encode(g, item.tile, scr);

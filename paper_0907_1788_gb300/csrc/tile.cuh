@@ -20,6 +20,7 @@
 // banks, and every per-register offset within a pass is a compile-time
 // constant.
 #pragma once
+#include "dbg.cuh"
 #include "field.cuh"
 
 namespace fntrs {
@@ -142,6 +143,11 @@ __device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restri
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, i2 = t / WT;
+    if constexpr (kDebugBounds && S::NP >= 2) {
+      if (!dbg_in(Y::addr(i2, c) + (R - 1) * Y::P1_STRIDE, Y::WORDS) ||
+          !dbg_in(i2 * R + R - 1, S::L))
+        continue;
+    }
     uint32_t x[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) x[q] = load(q * SP + i2, c);
@@ -166,6 +172,9 @@ __device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, g = t / WT;
     const int b = g / SP, i2 = g % SP;
+    if (!dbg_in(b * Y::MID_B + Y::addr(i2, c) + (R - 1) * Y::MID_STRIDE, Y::WORDS) ||
+        !dbg_in(i2 * R + R - 1, S::S1))
+      continue;
     uint32_t* base = sm + b * Y::MID_B + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
@@ -185,6 +194,7 @@ __device__ __forceinline__ void dif_last_sel(uint32_t* sm, Store& store) {
   constexpr int R = S::RL, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
+    if (!dbg_in(b * Y::LAST_B + c + (R - 1) * WT, Y::WORDS)) continue;
     const uint32_t* base = sm + b * Y::LAST_B + c;
     uint32_t x[R];
 #pragma unroll
@@ -213,6 +223,7 @@ __device__ __forceinline__ void dif_last_inplace(uint32_t* sm) {
   constexpr int R = S::RL, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
+    if (!dbg_in(b * Y::LAST_B + c + (R - 1) * WT, Y::WORDS)) continue;
     uint32_t* base = sm + b * Y::LAST_B + c;
     uint32_t x[R];
 #pragma unroll
@@ -232,6 +243,9 @@ __device__ __forceinline__ void dit_mid(uint32_t* sm, const uint32_t* __restrict
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, g = t / WT;
     const int b = g / SP, i2 = g % SP;
+    if (!dbg_in(b * Y::MID_B + Y::addr(i2, c) + (R - 1) * Y::MID_STRIDE, Y::WORDS) ||
+        !dbg_in(i2 * R + R - 1, S::S1))
+      continue;
     uint32_t* base = sm + b * Y::MID_B + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
@@ -254,6 +268,9 @@ __device__ __forceinline__ void dit_first(uint32_t* sm, const uint32_t* __restri
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, i2 = t / WT;
+    if (!dbg_in(Y::addr(i2, c) + (R - 1) * Y::P1_STRIDE, Y::WORDS) ||
+        !dbg_in(i2 * R + R - 1, S::L))
+      continue;
     const uint32_t* base = sm + Y::addr(i2, c);
     uint32_t x[R];
 #pragma unroll
@@ -276,6 +293,7 @@ __device__ __forceinline__ void dit_last_inplace(uint32_t* sm, const uint32_t* s
   for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
     const int c = t % WT, b = t / WT;
     const int off = b * Y::LAST_B + c;
+    if (!dbg_in(off + (R - 1) * WT, Y::WORDS)) continue;
     uint32_t x[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {

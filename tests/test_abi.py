@@ -38,6 +38,12 @@ def test_strerror_without_gpu():
 
     assert pkg.fnt_rs_strerror(0) == "ok"
     assert "65537" in pkg.fnt_rs_strerror(-2)
+    assert "debug build" in pkg.fnt_rs_strerror(pkg.E_BOUNDS)
+
+
+def test_release_build_has_no_device_index_checks(lib):
+    # the checks of the debug build (-DFNTRS_DEBUG_BOUNDS=1) are compiled out here
+    assert lib.fnt_rs_debug_bounds() == 0
 
 
 def test_argument_errors_without_gpu():
