@@ -7,9 +7,11 @@ n-k positions per batch): encode the batch, build the pattern's decode plan
 arrival order, the packed layout of the C ABI).
 
 value = source bytes (k * W * 2) round-tripped per second (encode + plan +
-decode), summed over ranks.  Per-step CUDA-event times exclude the L2 flush
-that separates steps (a 256 MB write).  `--impl reference` times the CPU
-oracle on a bounded sample of the same workload.
+decode), summed over ranks.  The timed steps run back to back with no L2
+flush over source, encoded and decoded buffers that rotate over more memory
+than L2 holds, so each step pays for its own write-back; a flushed pass is
+reported beside it.  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -81,7 +83,7 @@ def encode_instr(n: int, k: int) -> float:
 # k_plan_fused, k_decode_tma at n = 8192): the kernel templates, the headers they
 # include and the translation unit that instantiates them.
 KERNEL_SOURCES = ("field.cuh", "tile.cuh", "kernels.cuh", "kargs.h", "logplan.cuh", "tma.cuh",
-                  "sched.h", "inst.cuh", "inst_big.cu")
+                  "sched.h", "inst.cuh", "inst_big.cu", "dbg.cuh")
 
 
 def _src_hash() -> str:
@@ -746,9 +748,11 @@ def run_gpu(args):
     plan = pkg.Plan(n, k, device=dev)
 
     # schedules: time every one that can run this workload and keep the fastest
+    # (--no-autotune keeps the default schedules, e.g. under a profiler, whose
+    # serialised launches would skew the tuner's timings)
     tuned = {}
     for name, op in (("encode", pkg.OP_ENCODE), ("decode", pkg.OP_DECODE)):
-        res = plan.autotune(W, op, stream)
+        res = [] if args.no_autotune else plan.autotune(W, op, stream)
         tuned[name] = {"timed_us": {pkg.SCHED_NAMES[s_]: round(us, 2) for s_, us in res},
                        "chosen": pkg.SCHED_NAMES[plan.schedule(op)]}
 
@@ -1045,6 +1049,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged and serving runs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default schedules instead of timing every candidate")
     ap.add_argument("--ragged-groups", type=int, default=0,
                     help="groups of the seed-4 ragged batch to run (0: all 4096)")
     ap.add_argument("--serving-requests", type=int, default=3000,
