@@ -615,6 +615,73 @@ struct NopStore {
   __device__ __forceinline__ void operator()(int, int, uint32_t) const {}
 };
 
+// ---------------------------------------------------------------------------
+// Local pass of a split transform fused with the cross pass of the next one
+// (n = C * L, L = 4096 as 16 * 16 * 16, C in {4, 8, 16}).  Block j1 of the
+// current transform yields X[j1 + C j'] for j' < L; the next transform's cross
+// DFT for i2 (inputs at rows q L + i2, q < C) needs exactly the outputs of
+// block j1 = i2 mod C at j' = i2 div C + q (L / C).  In the last radix-16 pass
+// a task holds the 16 outputs j' = j0 + 256 t (t < 16, j0 < 256), which are
+// 16 / C such groups (t = g + (16 / C) u, u < C): the task runs those C-point
+// DFTs right away, in registers, instead of writing the local outputs to
+// global memory and reading them back in a separate cross pass.  Before the
+// cross DFT the values at full indices s >= row_limit are zeroed (the
+// truncation to j < k between D1 and D2) and, with AHAT, multiplied by ahat[s]
+// (the pointwise product between D2 and D3).  Output: rows j1'' L + i2 of out2
+// (ld_work), the same layout the cross pass writes.  Used by the persistent
+// ragged kernel's split items, whose cross passes one CTA runs alone (as a
+// separate pass each is bound by memory latency); the standalone split path
+// keeps separate cross kernels (fused there it measured 1.38 against 1.33 ms
+// at k = 32768, n = 65536, W = 1024: its cross kernels are cheap, many small
+// CTAs per SM).
+// ---------------------------------------------------------------------------
+template <class S, int WT, int NT, bool INV_LOCAL, int C, bool INV_CROSS, bool AHAT,
+          bool CG = false>
+__device__ __forceinline__ void local_cross_last(const uint32_t* sm, const KArgs& a, int j1,
+                                                 int col0) {
+  static_assert(S::NP == 3 && S::RL == 16 && S::L == 4096 && (C == 4 || C == 8 || C == 16), "");
+  using Y = Lay<S, WT>;
+  constexpr int R = 16, G = 16 / C, B = 4, BC = ilog2(C);
+  const uint32_t* pw = INV_CROSS ? a.powi : a.powf;
+  uint32_t* out = static_cast<uint32_t*>(a.out2);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, b = t / WT;
+    const int col = col0 + c;
+    if (!dbg_in(b * Y::LAST_B + c + (R - 1) * WT, Y::WORDS)) continue;
+    const uint32_t* base = sm + b * Y::LAST_B + c;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = base[q * WT];
+    dft_reg<R, INV_LOCAL>(x);
+    if (col >= a.W) continue;
+    const int j0 = S::natural(b * R);  // register q holds j' = j0 + 256 bitrev(q)
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int m = j0 + 256 * g;   // j' = m + (L / C) u
+      const int i2 = j1 + C * m;    // the next transform's cross index
+      uint32_t y[C];
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        uint32_t v = x[bitrev(g + G * u, B)];
+        const int srow = i2 + S::L * u;  // full index of this value
+        if constexpr (AHAT) v = m_mul(v, ld_tab<CG>(a.ahat + srow));
+        y[u] = srow < a.row_limit ? v : 0u;
+      }
+      dft_reg<C, INV_CROSS>(y);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const int jn = bitrev(r, BC);  // the next transform's local block
+        uint32_t v = y[r];
+        if (jn != 0) v = m_mul(v, __ldg(pw + (((long long)i2 * jn) & (a.n - 1))));
+        if (!dbg_in((long long)jn * S::L + i2, a.n, a.status)) continue;
+        out[((size_t)jn * S::L + i2) * a.ld_work + col] = v;
+      }
+    }
+  }
+}
+
+
+
 template <class S, int WT, int NT, bool CG = false>
 __device__ __forceinline__ void decode_body(const KArgs& a, int tx) {
   extern __shared__ uint4 smem_raw[];

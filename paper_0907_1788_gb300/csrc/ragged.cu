@@ -381,11 +381,15 @@ int fnt_rs_ragged_create(fnt_rs_ragged* out, const fnt_rs_group* groups, uint32_
     for (int gi = 0; gi < (int)pers.size(); ++gi) {
       dg.push_back(make_dev_group(r->groups[pers[gi]]));
       if (pers[gi] == stall) dg.back().enc_need += 1;
-      for (int t = 0; t < dg.back().enc_tiles; ++t) items.push_back({RI_ENC, gi, t});
     }
-    // a long code's spectrum item precedes the digit items that read it
+    // Order: the long codes' spectrum items (they wait on nothing), every
+    // encode tile, every pattern item, every decode tile.  The encode tiles
+    // between the spectra and the digit items that read them give the spectra
+    // time to finish, so digit items seldom wait.
     for (int gi = 0; gi < (int)pers.size(); ++gi)
       if (dg[gi].has_plan && dg[gi].long_plan) items.push_back({RI_SPEC, gi, 0});
+    for (int gi = 0; gi < (int)pers.size(); ++gi)
+      for (int t = 0; t < dg[gi].enc_tiles; ++t) items.push_back({RI_ENC, gi, t});
     for (int gi = 0; gi < (int)pers.size(); ++gi)
       if (dg[gi].has_plan)
         for (int t = 0; t < dg[gi].plan.D; ++t) items.push_back({RI_PLAN, gi, t});

@@ -4,9 +4,10 @@
 // items in list order from an atomic counter.
 //
 // How a group's work is cut depends on its length:
-//   tile  (n <= 32768; decode n <= 16384 or k <= n/2): one CTA holds a whole
-//         codeword tile in shared memory, as the standalone tile kernels do;
-//   split (encode n = 65536; decode n = 65536, or n = 32768 with k > n/2): a
+//   tile  (encode n <= 16384; decode n <= 16384, or n = 32768 with k <= n/2):
+//         one CTA holds a whole codeword tile in shared memory, as the
+//         standalone tile kernels do;
+//   split (encode n >= 32768; decode n = 65536, or n = 32768 with k > n/2): a
 //         work item is a tile of up to 8 columns, and its CTA runs the whole
 //         split transform of those columns itself (radix-n/4096 cross pass
 //         into its own global scratch, then the n/4096 local 4096-point
@@ -95,7 +96,7 @@ int launch_ragged(const RaggedArgs& ra, int grid, cudaStream_t st);
 int ragged_wt_enc(int L);
 int ragged_wt_dec(int L, bool blocked);
 // Which groups run the in-CTA split transform, and which build long patterns.
-inline bool ragged_split_enc(int L) { return L > 32768; }
+inline bool ragged_split_enc(int L) { return L >= 32768; }
 inline bool ragged_split_dec(int L, bool blocked) { return L > 32768 || (L == 32768 && blocked); }
 inline bool ragged_long_plan(int L) { return L >= 32768; }
 

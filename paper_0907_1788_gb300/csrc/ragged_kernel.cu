@@ -1,10 +1,10 @@
 // The ragged persistent kernel: one launch runs the encode tiles, pattern
 // builds and decode tiles of every group with n >= 256 in a ragged batch.
 // CTAs stay resident and take work items in list order from an atomic
-// counter; the list puts all encode, spectrum and pattern items before the
-// decode items (and every spectrum item before the digit items that read
-// it), so an item only ever waits (boundedly) on items that running CTAs
-// already hold, and every wait ends.  Data written by other CTAs of the same
+// counter; the list puts the spectrum items first, then all encode and
+// pattern items, then the decode items (every spectrum item before the digit
+// items that read it), so an item only ever waits (boundedly) on items that
+// running CTAs already hold, and every wait ends.  Data written by other CTAs of the same
 // launch (encoded rows, pattern tables, spectra) is read through L2 only.
 #include <cuda_runtime.h>
 
@@ -121,17 +121,57 @@ __device__ void cross_rt(const KArgs& x, bool inv, int lm) {
   __syncthreads();
 }
 
-template <bool INV>
+// MODE < 0: the output mode is read at run time (x.mode; the rarer modes share
+// one body per direction); the frequent ones have bodies of their own.
+template <bool INV, int MODE>
 __device__ __noinline__ void cta_local(const KArgs& x) {
   for (int j1 = 0; j1 < x.C; ++j1) {
-    tile_body<SLoc, WL, NT, INV, LoadRows32<WL>, StoreLocalRT<WL, true>>(x, 0, j1);
+    if constexpr (MODE < 0)
+      tile_body<SLoc, WL, NT, INV, LoadRows32<WL>, StoreLocalRT<WL, true>>(x, 0, j1);
+    else
+      tile_body<SLoc, WL, NT, INV, LoadRows32<WL>, StoreLocal<WL, MODE>>(x, 0, j1);
     __syncthreads();
   }
 }
 
 __device__ void local_rt(const KArgs& x, bool inv) {
-  if (inv) cta_local<true>(x);
-  else cta_local<false>(x);
+  if (!inv && x.mode == LM_ENC) cta_local<false, LM_ENC>(x);
+  else if (inv && x.mode == LM_OUT16) cta_local<true, LM_OUT16>(x);
+  else if (inv) cta_local<true, -1>(x);
+  else cta_local<false, -1>(x);
+}
+
+// The C local passes of one transform, each fused with the next transform's
+// cross DFTs (local_cross_last): reads x.in (rows j1 * 4096 + i), writes the
+// next transform's cross output to x.out2.  which = 0: D1 local (inverse),
+// truncation at x.row_limit, D2 cross (forward); which = 1: D2 local (forward)
+// * ahat, D3 cross (inverse).
+template <int C, int WHICH>
+__device__ __noinline__ void cta_local_cross(const KArgs& x) {
+  constexpr bool INV_LOCAL = WHICH == 0, INV_CROSS = WHICH == 1, AHAT = WHICH == 1;
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
+  const uint32_t* tw = INV_LOCAL ? x.twi : x.twf;
+  for (int j1 = 0; j1 < C; ++j1) {
+    LoadRows32<WL> load = LoadRows32<WL>::make(x, 0, j1);
+    NopStore nop;
+    dif_first<SLoc, WL, NT, INV_LOCAL>(sm, tw, load, nop);
+    __syncthreads();
+    dif_mid<SLoc, WL, NT, INV_LOCAL>(sm, tw + SLoc::TW2_OFF);
+    mid_last_sync<SLoc, WL, NT>();
+    local_cross_last<SLoc, WL, NT, INV_LOCAL, C, INV_CROSS, AHAT, true>(sm, x, j1, 0);
+    __syncthreads();
+  }
+}
+
+__device__ void local_cross_rt(const KArgs& x, int which) {
+  if (x.C == 16) {
+    if (which == 0) cta_local_cross<16, 0>(x);
+    else cta_local_cross<16, 1>(x);
+  } else {
+    if (which == 0) cta_local_cross<8, 0>(x);
+    else cta_local_cross<8, 1>(x);
+  }
 }
 
 // Encode of columns [tile*WL, +WL) of a long code (Sec. II.B: e = FNT of the
@@ -192,12 +232,19 @@ __device__ void split_decode(const RaggedGroupDev& g, int tile, uint32_t* scr) {
     x.mode = mode;
     local_rt(x, inv);
   };
+  // a local pass fused with the next transform's cross pass (4 passes, not 6)
+  auto local_cross = [&](int which, const uint32_t* in, uint32_t* o2, int row_limit) {
+    KArgs x = c;
+    x.in = in;
+    x.ld_in = (size_t)w;
+    x.out2 = o2;
+    x.row_limit = row_limit;
+    local_cross_rt(x, which);
+  };
   if (!g.blocked) {
     cross(true, CL_RECV, recv, g.dec.ld_in, n);
-    local(true, LM_WORK, B0, nullptr, k, nullptr);
-    cross(false, CL_U32, B0, (size_t)w, k);
-    local(false, LM_WORK_AHAT, B0, nullptr, n, nullptr);
-    cross(true, CL_U32, B0, (size_t)w, n);
+    local_cross(0, A, B0, k);
+    local_cross(1, B0, A, n);
     local(true, LM_OUT16, nullptr, nullptr, k, nullptr);
   } else {
     cross(true, CL_RECV, recv, g.dec.ld_in, n);
@@ -382,7 +429,7 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(RaggedArgs ra) {
         split_encode(g, item.tile, scr);
       } else {
 #define FNTRS_CALL(X) rg_encode<X>(g.enc, item.tile)
-        FNTRS_RAGGED_SWITCH(L, FNTRS_CALL)
+        FNTRS_RAGGED_SWITCH_FUSED(L, FNTRS_CALL)  // tile encodes: n <= 16384
 #undef FNTRS_CALL
       }
       __threadfence();
@@ -478,7 +525,7 @@ int ragged_wt_enc(int L) {
     case 4096: return wt_one(4096);
     case 8192: return wt_one(8192);
     case 16384: return wt_one(16384);
-    case 32768: return wt_one(32768);
+    case 32768: return kRaggedSplitWT;
     case 65536: return kRaggedSplitWT;
     default: return 0;
   }
@@ -486,7 +533,19 @@ int ragged_wt_enc(int L) {
 
 int ragged_wt_dec(int L, bool blocked) {
   if (ragged_split_dec(L, blocked)) return kRaggedSplitWT;
-  if (!blocked) return ragged_wt_enc(L);
+  if (!blocked) {  // the one-CTA tile bodies (the encode of 32768 is split, this decode not)
+    switch (L) {
+      case 256: return wt_one(256);
+      case 512: return wt_one(512);
+      case 1024: return wt_one(1024);
+      case 2048: return wt_one(2048);
+      case 4096: return wt_one(4096);
+      case 8192: return wt_one(8192);
+      case 16384: return wt_one(16384);
+      case 32768: return wt_one(32768);
+      default: return 0;
+    }
+  }
   switch (L) {
     case 256: return wt_two(256);
     case 512: return wt_two(512);
