@@ -215,7 +215,7 @@ int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st)
   const int nwide = (a.W + WT - 1) / WT;
   const int nfull = tail_full_tiles(nwide, t.sms * occ[dev & 63], WT);
   const int grid = nfull + 2 * (nwide - nfull);  // one CTA per tile (see clc_take)
-  kern<<<grid, NT, smem, st>>>(a, t.pat32, t.rows_staged, t.box_rows, nfull,
+  kern<<<grid, NT, smem, st>>>(a, t.rowtab, t.rows_staged, t.box_rows, nfull,
                                *static_cast<const CUtensorMap*>(t.map));
   count_launch();
   return 0;

@@ -29,6 +29,7 @@ struct PatternSlot {
   uint32_t* ahat = nullptr;
   uint32_t* ahat2 = nullptr;
   uint32_t* pat32 = nullptr;  // (row << 17) | weight per position
+  uint32_t* rowtab = nullptr;  // (position << 17) | weight per received row (first k rows)
   uint32_t* pos_d = nullptr;  // first k positions (device)
   uint32_t* pos_h = nullptr;  // pinned staging of the upload
   const uint32_t* pos_map = nullptr;  // pos_h as seen from the device (mapped pinned memory)

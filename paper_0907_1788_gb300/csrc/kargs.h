@@ -86,6 +86,7 @@ struct PlanArgs {
   uint32_t* conv = nullptr;        // [n][D] digit convolutions (scratch)
   uint2* pat = nullptr;            // position table (written)
   uint32_t* pat32 = nullptr;
+  uint32_t* rowtab = nullptr;  // per received row, or null
   uint32_t* aval = nullptr;        // A(r^j) (split step-6 product) or null
   uint32_t* ahat = nullptr;        // n^-1 FNT(A mod x^k) or null
   uint32_t* done = nullptr;        // CTA completion counter, zero between builds

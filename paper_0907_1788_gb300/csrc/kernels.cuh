@@ -116,6 +116,54 @@ struct LoadRecv {
   }
 };
 
+// N consecutive words at p (aligned to min(4N, 16) bytes) in the widest
+// accesses that alignment allows; the stores are streaming (evict-first).
+template <int N>
+__device__ __forceinline__ void ld_words(const uint32_t* p, uint32_t (&v)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int u = 0; u < N / 4; ++u) {
+      const uint4 t = reinterpret_cast<const uint4*>(p)[u];
+      v[4 * u] = t.x, v[4 * u + 1] = t.y, v[4 * u + 2] = t.z, v[4 * u + 3] = t.w;
+    }
+  } else if constexpr (N == 2) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = p[c];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&v)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int u = 0; u < N / 4; ++u)
+      reinterpret_cast<uint4*>(p)[u] = make_uint4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+  } else if constexpr (N == 2) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) p[c] = v[c];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void st_words_cs(uint32_t* p, const uint32_t (&v)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int u = 0; u < N / 4; ++u)
+      __stcs(reinterpret_cast<uint4*>(p) + u,
+             make_uint4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]));
+  } else if constexpr (N == 2) {
+    __stcs(reinterpret_cast<uint2*>(p), make_uint2(v[0], v[1]));
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) __stcs(p + c, v[c]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Storers: spectrum index j of tile codeword c.
 // ---------------------------------------------------------------------------
@@ -568,10 +616,49 @@ struct StoreOut16 {
   int* status;
   int col0, W, k;
   uint32_t bad;
+  bool vec;  // row segments of WT columns start on a boundary of their own size (<= 16 bytes)
   static __device__ __forceinline__ StoreOut16 make(const KArgs& a, int tx, int ty) {
     (void)ty;
+    const int vb = a.out32 ? (4 * WT < 16 ? 4 * WT : 16) : (2 * WT < 16 ? 2 * WT : 16);
+    const int es = a.out32 ? 4 : 2;
+    const uintptr_t base = a.out32 ? (uintptr_t)a.out32 : (uintptr_t)a.out;
+    const bool vec = base % vb == 0 && (a.ld_out * es) % vb == 0;
     return StoreOut16{static_cast<uint16_t*>(a.out), static_cast<uint32_t*>(a.out32), a.ld_out,
-                      a.status, tx * WT, a.W, a.k, 0u};
+                      a.status, tx * WT, a.W, a.k, 0u, vec};
+  }
+  // the WT columns col0.. of row j < k at once, values already in [0, p): one
+  // wide store when the segment is aligned and inside the matrix
+  // (as operator(): 65536 is out of range only for the 16-bit symbols)
+  __device__ __forceinline__ void row(int j, const uint32_t (&v)[WT]) {
+    const bool whole = vec && col0 + WT <= W;
+    if (out32) {
+      uint32_t* p = out32 + (size_t)j * ld + col0;
+      if (whole) {
+        st_words_cs<WT>(p, v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < WT; ++c)
+          if (col0 + c < W) __stcs(p + c, v[c]);
+      }
+      return;
+    }
+    uint32_t m = v[0];
+#pragma unroll
+    for (int c = 1; c < WT; ++c) m = max(m, v[c]);
+    bad = max(bad, m);
+    uint16_t* p = out + (size_t)j * ld + col0;
+    if constexpr (WT >= 2) {
+      if (whole) {
+        uint32_t h[WT / 2];
+#pragma unroll
+        for (int u = 0; u < WT / 2; ++u) h[u] = __byte_perm(v[2 * u], v[2 * u + 1], 0x5410);
+        st_words_cs<WT / 2>(reinterpret_cast<uint32_t*>(p), h);
+        return;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < WT; ++c)
+      if (col0 + c < W) __stcs(p + c, (uint16_t)v[c]);
   }
   __device__ __forceinline__ void operator()(int j, int c, uint32_t v) {
     const int col = col0 + c;
@@ -784,11 +871,13 @@ __global__ void __launch_bounds__(NT) k_decode(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused decode with TMA-staged received rows (packed layout: row i of recv
-// holds the symbols of positions[i]; n = L, k <= n/2).  One CTA per tile of WT
-// codewords, tiles of CTAs not yet launched taken over as in k_encode_tma.  Same
-// transform sequence as k_decode; pass 1 gathers u[z] = v_row(z) * c_z from the
-// staged [k][WT] tile through pat32[z] = (row << 17) | c_z (c_z = 0: unused).
+// Fused decodes of staged received rows (packed layout: row i of recv holds
+// the symbols of positions[i]; n = L, k <= n/2), one CTA per tile of WT
+// codewords.  Same transform sequence as k_decode.  k_decode_tma (TMA stage,
+// tiles of CTAs not yet launched taken over as in k_encode_tma) scatters the
+// staged rows into the work buffer through rowtab[i] = (z_i << 17) | c_i;
+// k_decode_cpa (cp.async stage) gathers u[z] = v_row(z) * c_z in pass 1
+// through pat32[z] = (row << 17) | c_z (c_z = 0: unused).
 // smem: work (Lay WORDS u32) | stage (rows_staged * WT u32) | mbarrier.
 // ---------------------------------------------------------------------------
 // (WT = the stage's row stride; `stage` may point at a column inside the row)
@@ -808,26 +897,20 @@ struct LoadStaged {
   }
 };
 
-// Steps 4-6 (Sec. II.B) on one staged tile of WT codewords, n = L, k <= n/2:
-// D1 = FNT with root r^-1 of u (pass 1 reads the stage through `load`),
-// truncation to j < k, D2 = FNT with root r, * ahat, D3 = FNT with root r^-1
-// to `store`; boundary passes of consecutive transforms fused.  `freed()` runs
-// (in every thread, after a barrier) once pass 1 has read the whole stage.
+// Steps 4-6 (Sec. II.B) on one staged tile of WT codewords, n = L, k <= n/2,
+// after the first D1 pass (root r^-1) has left its output in the slots:
+// the other D1 passes, truncation to j < k, D2 = FNT with root r, * ahat and
+// every D3 pass (root r^-1) but the last; boundary passes of consecutive
+// transforms fused.
 // HALF (k = n/2 exactly): the truncation keeps the even registers of the
 // last D1 pass, so the first D2 pass sees a zero upper half, and D3 stores
 // only j < n/2; the compiler drops the butterfly halves nobody reads.
-template <class S, int WT, int NT, bool HALF, class LD, class ST, class F>
-__device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& store,
-                                                   const KArgs& a, F&& freed) {
+template <class S, int WT, int NT, bool HALF>
+__device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) {
   using Y = Lay<S, WT>;
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
   const uint32_t* __restrict__ ahat = a.ahat;
-  NopStore nop;
-  // D1 pass 1 (root r^-1) from the stage
-  dif_first<S, WT, NT, true>(sm, tw1i, load, nop);
-  __syncthreads();
-  freed();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
     mid_last_sync<S, WT, NT>();  // the last pass reads only its group's blocks
@@ -892,7 +975,104 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
     mid_last_sync<S, WT, NT>();
   }
+}
+
+// The whole decode of one staged tile, the first pass gathering its input
+// through `load` (LoadStaged), the last one handing spectrum index j < k to
+// `store`.  `freed()` runs (in every thread, after a barrier) once pass 1 has
+// read the whole stage.
+template <class S, int WT, int NT, bool HALF, class LD, class ST, class F>
+__device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& store,
+                                                   const KArgs& a, F&& freed) {
+  NopStore nop;
+  dif_first<S, WT, NT, true>(sm, a.twi, load, nop);
+  __syncthreads();
+  freed();
+  decode_mid_passes<S, WT, NT, HALF>(sm, a);
   dif_last_sel<S, WT, NT, true, HALF>(sm, store);
+}
+
+// Steps 4 and 5 (Sec. II.B) for a staged tile, row by row: u[z_i] = v_i c_i
+// for each of the first k received rows i (z_i, c_i from rowtab[i]), written
+// at the natural-order address of position z_i; the other positions of the
+// buffer are zero already.  Stage row i: WT words at stage + i * sw.
+template <class S, int WT, int NT>
+__device__ __forceinline__ void scatter_received(uint32_t* sm, const uint32_t* stage, int sw,
+                                                 const uint32_t* __restrict__ rowtab, int k,
+                                                 uint32_t& vmax) {
+  using Y = Lay<S, WT>;
+  // U rows per thread per round, their table entries loaded together (one
+  // memory latency per round instead of one per row)
+  constexpr int U = WT <= 8 ? 8 : 32 / WT;
+  for (int i0 = threadIdx.x; i0 < k; i0 += U * NT) {
+    uint32_t e[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * NT;
+      e[u] = i < k ? __ldg(rowtab + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * NT;
+      const int z = (int)(e[u] >> 17);
+      const uint32_t w = e[u] & 0x1FFFFu;
+      if (i >= k || !dbg_in(z, S::L)) continue;
+      uint32_t v[WT];
+      ld_words<WT>(stage + (size_t)i * sw, v);
+#pragma unroll
+      for (int c = 0; c < WT; ++c) {
+        vmax = max(vmax, v[c]);
+        v[c] = m_mul(v[c], w);
+      }
+      st_words<WT>(sm + Y::addr(z, 0), v);
+    }
+  }
+}
+
+// Output of a tile after dif_last_reduce: rows j < k, the WT codewords of a
+// row read from its slot at once and stored by `store.row`; the slot is
+// zeroed again, so that the whole buffer is zero when the next tile's
+// received rows are scattered into it.  HALF (k = L/2): the slots with last
+// digit below RL/2, taken in order (consecutive threads, consecutive slots).
+template <class S, int WT, int NT, bool HALF>
+__device__ __forceinline__ void copy_out(uint32_t* sm, StoreOut16<WT>& store, int k) {
+  using Y = Lay<S, WT>;
+  constexpr int R = S::RL, H = R / 2;
+  constexpr int M = HALF ? S::L / 2 : S::L;
+  for (int m = threadIdx.x; m < M; m += NT) {
+    const int slot = HALF ? (m / H) * R + m % H : m;
+    const int j = S::natural(slot);
+    if (!HALF && j >= k) continue;
+    if (!dbg_in(Y::addr(slot, WT - 1), Y::WORDS)) continue;
+    uint32_t* p = sm + Y::addr(slot, 0);
+    uint32_t v[WT], zero[WT];
+    ld_words<WT>(p, v);
+#pragma unroll
+    for (int c = 0; c < WT; ++c) zero[c] = 0u;
+    st_words<WT>(p, zero);
+    store.row(j, v);
+  }
+}
+
+// The decode of one staged tile with the received rows scattered into the
+// (all-zero) work buffer first: `freed()` runs (in every thread, after a
+// barrier) as soon as the scatter has read the stage; the first D1 pass then
+// works in place, and the last D3 pass writes back reduced values for
+// copy_out, which leaves the buffer zero again.
+template <class S, int WT, int NT, bool HALF, class F>
+__device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t* stage, int sw,
+                                                    const uint32_t* __restrict__ rowtab,
+                                                    uint32_t& vmax, StoreOut16<WT>& store,
+                                                    const KArgs& a, F&& freed) {
+  scatter_received<S, WT, NT>(sm, stage, sw, rowtab, a.k, vmax);
+  __syncthreads();
+  freed();
+  dif_first_inplace<S, WT, NT, true>(sm, a.twi);
+  __syncthreads();
+  decode_mid_passes<S, WT, NT, HALF>(sm, a);
+  dif_last_reduce<S, WT, NT, true, HALF>(sm, a.k);
+  __syncthreads();
+  copy_out<S, WT, NT, HALF>(sm, store, a.k);
 }
 
 // Tiles: the first `nfull` tiles are WT codewords wide; the columns after them
@@ -902,7 +1082,7 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
 // WT wide.
 template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT, 1)
-    k_decode_tma(KArgs a, const uint32_t* __restrict__ pat32, int rows_staged, int box_rows,
+    k_decode_tma(KArgs a, const uint32_t* __restrict__ rowtab, int rows_staged, int box_rows,
                  int nfull, const __grid_constant__ CUtensorMap trecv) {
   static_assert(S::NP >= 2, "");
   dbg_enter(a.status);
@@ -928,6 +1108,8 @@ __global__ void __launch_bounds__(NT, 1)
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
   }
+  // the work buffer starts all zero (decode_scatter_tile keeps it so)
+  for (int i = threadIdx.x; i < WORK_BYTES / 16; i += NT) smem_raw[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   if (threadIdx.x == 0 && tile < ntiles) {
     mbar_expect_tx(bar, tx_bytes);
@@ -937,7 +1119,7 @@ __global__ void __launch_bounds__(NT, 1)
   }
   uint32_t parity = 0, cphase = 0;
   bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
-  LoadStaged<WT> load{stage, pat32, 0u, rows_staged};
+  uint32_t vmax = 0u;  // largest received value seen (> 65536 is out of range)
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
   auto freed = [&]() {
@@ -975,21 +1157,20 @@ __global__ void __launch_bounds__(NT, 1)
       if (tile >= nfull) {
         // a half tile: columns (tile - nfull) & 1 of its box, WH codewords
         const int h = tile - nfull;
-        LoadStaged<WT> lh{stage + (h & 1) * WH, pat32, load.vmax, rows_staged};
         store_h.col0 = nfull * WT + h * WH;
-        decode_staged_tile<S, WH, NT, HALF>(sm, lh, store_h, a, freed);
-        load.vmax = lh.vmax;
+        decode_scatter_tile<S, WH, NT, HALF>(sm, stage + (h & 1) * WH, WT, rowtab, vmax, store_h,
+                                             a, freed);
         __syncthreads();
         tile = s_next;
         continue;
       }
     }
     store.col0 = tile * WT;
-    decode_staged_tile<S, WT, NT, HALF>(sm, load, store, a, freed);
+    decode_scatter_tile<S, WT, NT, HALF>(sm, stage, WT, rowtab, vmax, store, a, freed);
     __syncthreads();
     tile = s_next;
   }
-  if (load.vmax > 65536u) atomicOr(a.status, ST_RANGE);
+  if (vmax > 65536u) atomicOr(a.status, ST_RANGE);
   store.flush();
   store_h.flush();
 }
@@ -1356,7 +1537,8 @@ __device__ __forceinline__ bool plan_body(const PlanArgs& pa, int t) {
   __syncthreads();  // s_last is rewritten by the next build this CTA runs
   if (!last) return false;
   __threadfence();
-  const LogFinal f{pa.conv, pa.D, pa.b, L, k, pa.exp3, pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat};
+  const LogFinal f{pa.conv, pa.D, pa.b, L,       k,       pa.exp3, pa.ninv,
+                   pa.pat,  pa.pat32, pa.aval, pa.ahat, pa.rowtab};
   lg_final_block<L, NT>(f);
   if (threadIdx.x == 0) *pa.done = 0u;
   return true;

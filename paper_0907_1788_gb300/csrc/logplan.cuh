@@ -23,6 +23,7 @@ struct LogFinal {
   uint32_t* pat32;  // (row << 17) | weight, 0 for erased positions
   uint32_t* aval;   // A(r^j) or null
   uint32_t* ahat;   // n^-1 FNT(A mod x^k) or null
+  uint32_t* rowtab = nullptr;  // (j << 17) | weight at index row, or null
 };
 
 // exp3 index of position j: the weight's exponent (received) or log A(r^j) (erased)
@@ -49,6 +50,7 @@ __device__ __forceinline__ void lg_store(const LogFinal& f, int j, uint32_t row,
     const uint32_t c = kP - x;
     f.pat[j].y = c;
     f.pat32[j] = (row << 17) | c;
+    if (f.rowtab) f.rowtab[row] = ((uint32_t)j << 17) | c;
   } else {
     f.pat32[j] = 0u;
     A = x;

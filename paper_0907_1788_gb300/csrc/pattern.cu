@@ -201,12 +201,15 @@ __global__ void k_lg_scale2(const uint32_t* __restrict__ E, int n, uint32_t ninv
   ahat2[j] = p_mul(E[(size_t)j * 2 + 1], ninv);
 }
 
-// compact per-position entry (row << 17) | weight for the staged decode
-__global__ void k_pat32(const uint2* __restrict__ pat, uint32_t* __restrict__ pat32, int n) {
+// compact per-position entry (row << 17) | weight for the staged decode, and
+// the per-row entry (position << 17) | weight of each received row
+__global__ void k_pat32(const uint2* __restrict__ pat, uint32_t* __restrict__ pat32,
+                        uint32_t* __restrict__ rowtab, int n) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z < n) {
     const uint2 e = pat[z];
     pat32[z] = e.y ? ((e.x << 17) | e.y) : 0u;
+    if (e.y && rowtab && e.x < (uint32_t)n) rowtab[e.x] = ((uint32_t)z << 17) | e.y;
   }
 }
 
@@ -214,8 +217,8 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
-void launch_pat32(const uint2* pat, uint32_t* pat32, int n, cudaStream_t st) {
-  k_pat32<<<blocks_for(n, 256), 256, 0, st>>>(pat, pat32, n);
+void launch_pat32(const uint2* pat, uint32_t* pat32, uint32_t* rowtab, int n, cudaStream_t st) {
+  k_pat32<<<blocks_for(n, 256), 256, 0, st>>>(pat, pat32, rowtab, n);
   count_launch();
 }
 
@@ -234,8 +237,8 @@ void launch_lg_mul(const uint32_t* spec, const uint32_t* ghat, int D, int n, uin
 }
 void launch_lg_final(const uint32_t* conv, int D, int b, int n, int k, const uint32_t* exp3,
                      uint32_t ninv, uint2* pat, uint32_t* pat32, uint32_t* aval, uint32_t* ahat,
-                     cudaStream_t st) {
-  const LogFinal f{conv, D, b, n, k, exp3, ninv, pat, pat32, aval, ahat};
+                     uint32_t* rowtab, cudaStream_t st) {
+  const LogFinal f{conv, D, b, n, k, exp3, ninv, pat, pat32, aval, ahat, rowtab};
   k_lg_final<<<blocks_for(n, 256), 256, 0, st>>>(f);
   count_launch();
 }

@@ -96,8 +96,8 @@ void launch_lg_mul(const uint32_t* spec, const uint32_t* ghat, int D, int n, uin
                    cudaStream_t st);
 void launch_lg_final(const uint32_t* conv, int D, int b, int n, int k, const uint32_t* exp3,
                      uint32_t ninv, uint2* pat, uint32_t* pat32, uint32_t* aval, uint32_t* ahat,
-                     cudaStream_t st);
-void launch_pat32(const uint2* pat, uint32_t* pat32, int n, cudaStream_t st);
+                     uint32_t* rowtab, cudaStream_t st);
+void launch_pat32(const uint2* pat, uint32_t* pat32, uint32_t* rowtab, int n, cudaStream_t st);
 void launch_lg_halves(const uint32_t* coef, int n, int k, uint32_t* M, cudaStream_t st);
 void launch_lg_scale2(const uint32_t* E, int n, uint32_t ninv, uint32_t* ahat, uint32_t* ahat2,
                       cudaStream_t st);
@@ -407,6 +407,7 @@ int alloc_pattern_tables(PatternSlot& sl, size_t n, bool staging) {
   if (cudaMalloc(&sl.pat, n * sizeof(uint2)) != cudaSuccess ||
       cudaMalloc(&sl.ahat, n * 4) != cudaSuccess || cudaMalloc(&sl.ahat2, n * 4) != cudaSuccess ||
       cudaMalloc(&sl.pos_d, n * 4) != cudaSuccess || cudaMalloc(&sl.pat32, n * 4) != cudaSuccess ||
+      cudaMalloc(&sl.rowtab, n * 4) != cudaSuccess ||
       cudaMalloc(&sl.done, 4) != cudaSuccess || cudaMemset(sl.done, 0, 4) != cudaSuccess)
     return FNT_RS_E_CUDA;
   if (staging && (cudaMallocHost(&sl.pos_h, n * 4) != cudaSuccess ||
@@ -428,6 +429,7 @@ void free_pattern_tables(PatternSlot& sl) {
   cudaFree(sl.ahat2);
   cudaFree(sl.pos_d);
   cudaFree(sl.pat32);
+  cudaFree(sl.rowtab);
   cudaFree(sl.done);
   if (sl.pos_h) cudaFreeHost(sl.pos_h);
   if (sl.staged) cudaEventDestroy(sl.staged);
@@ -468,6 +470,7 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32
     pa.conv = conv;
     pa.pat = sl.pat;
     pa.pat32 = sl.pat32;
+    pa.rowtab = sl.rowtab;
     pa.aval = p->blocked ? aval : nullptr;
     pa.ahat = p->blocked ? nullptr : sl.ahat;
     pa.done = sl.done;
@@ -482,11 +485,11 @@ int build_pattern_log(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st, uint32
     if ((rc = run_fnt_default(n, P, D, conv, D, D, true, 1, work, st))) return rc;
     if (!p->blocked) {
       launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, nullptr,
-                      sl.ahat, st);
+                      sl.ahat, sl.rowtab, st);
       return cuda_ok(cudaGetLastError());
     }
     launch_lg_final(conv, D, p->lg_b, n, k, p->exp3, p->ninv, sl.pat, sl.pat32, aval, nullptr,
-                    st);
+                    sl.rowtab, st);
   }
   if ((rc = run_fnt_default(n, aval, 1, coef, 1, 1, true, 1, work, st))) return rc;
   launch_lg_halves(coef, n, k, M2, st);
@@ -552,7 +555,7 @@ int build_pattern(fnt_rs_plan_s* p, PatternSlot& sl, cudaStream_t st) {
   launch_pat_prep(lv[cur], k, n, ncols, n / 2, M, st);
   if ((rc = run_fnt_default(n, M, ncols, E, ncols, ncols, false, 1, work, st))) return rc;
   launch_pat_final(E, ncols, sl.pos_d, k, n, p->tn.powi, p->ninv, sl.pat, sl.ahat, sl.ahat2, st);
-  launch_pat32(sl.pat, sl.pat32, n, st);
+  launch_pat32(sl.pat, sl.pat32, sl.rowtab, n, st);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -819,6 +822,7 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   a.out32 = out32;
   TmaDecodeArgs t;
   t.pat32 = sl.pat32;
+  t.rowtab = sl.rowtab;
   t.rows_staged = rows_staged;
   t.box_rows = box_rows;
   t.sms = p->sms;

@@ -223,6 +223,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
     pa.conv = conv;
     pa.pat = rg.tab.pat;
     pa.pat32 = rg.tab.pat32;
+    pa.rowtab = rg.tab.rowtab;
     pa.aval = p->blocked ? lp.aval : nullptr;
     pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
     pa.done = rg.tab.done;
@@ -248,6 +249,7 @@ static RaggedGroupDev make_dev_group(const RaggedGroup& rg) {
   pa.conv = conv;
   pa.pat = rg.tab.pat;
   pa.pat32 = rg.tab.pat32;
+  pa.rowtab = rg.tab.rowtab;
   pa.aval = p->blocked ? aval : nullptr;
   pa.ahat = p->blocked ? nullptr : rg.tab.ahat;
   pa.done = rg.tab.done;

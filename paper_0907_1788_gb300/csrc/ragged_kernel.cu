@@ -339,7 +339,8 @@ __device__ __noinline__ bool rg_digit(const RaggedGroupDev& g, int t, uint32_t* 
   if (!last) return false;
   __threadfence();
   const int k = g.dec.k;
-  const LogFinal f{pa.conv, pa.D, pa.b, L, k, pa.exp3, pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat};
+  const LogFinal f{pa.conv, pa.D,     pa.b,    L,       k,        pa.exp3,
+                   pa.ninv, pa.pat, pa.pat32, pa.aval, pa.ahat, pa.rowtab};
   lg_final_block<L, NT>(f);
   if (g.blocked) {
     __syncthreads();

@@ -73,6 +73,7 @@ int launch_encode_tma(int L, int C, const KArgs& a, const TmaEncodeArgs& t, cuda
 // TMA-staged decode (n = L <= tile limit, k <= n/2, packed rows).
 struct TmaDecodeArgs {
   const uint32_t* pat32;
+  const uint32_t* rowtab;  // (position << 17) | weight of received row i < k
   int rows_staged, box_rows;
   int sms;          // SMs of the device (the launch sizes its last round of tiles by it)
   const void* map;  // CUtensorMap*

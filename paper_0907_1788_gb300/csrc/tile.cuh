@@ -48,6 +48,16 @@ struct Sched {
       return j1 + R1 * (rem / S2) + R1 * R2 * (rem % S2);
     }
   }
+  // the slot holding spectrum index j (the inverse of natural)
+  static __device__ __forceinline__ int slot_of(int j) {
+    if constexpr (NP == 1) {
+      return j;
+    } else if constexpr (NP == 2) {
+      return (j % R1) * S1 + j / R1;
+    } else {
+      return (j % R1) * S1 + ((j / R1) % R2) * S2 + j / (R1 * R2);
+    }
+  }
 };
 
 // Padded shared-memory layout of one [L][WT] buffer.
@@ -164,6 +174,29 @@ __device__ __forceinline__ void dif_first(uint32_t* sm, const uint32_t* __restri
   }
 }
 
+// DIF pass 1 in place: input element i of codeword c at the natural-order
+// address Lay::addr(i, c).  Task (i2, c) reads i = q*S1 + i2 (q < R1) and
+// writes the slots bitrev(q)*S1 + i2, the same addresses (S1 is a multiple of
+// the last radix, so addr(q*S1 + i2) = addr(i2) + q*P1_STRIDE).
+template <class S, int WT, int NT, bool INV>
+__device__ __forceinline__ void dif_first_inplace(uint32_t* sm, const uint32_t* __restrict__ tw) {
+  static_assert(S::NP >= 2 && S::S1 % S::RL == 0, "");
+  using Y = Lay<S, WT>;
+  constexpr int R = S::R1, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, i2 = t / WT;
+    if (!dbg_in(Y::addr(i2, c) + (R - 1) * Y::P1_STRIDE, Y::WORDS)) continue;
+    uint32_t* base = sm + Y::addr(i2, c);
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = base[q * Y::P1_STRIDE];
+    dft_reg<R, INV>(x);
+    twiddle_regs<R>(x, tw + i2 * R);
+#pragma unroll
+    for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
+  }
+}
+
 // DIF pass 2 of a 3-pass schedule, slots -> slots.
 template <class S, int WT, int NT, bool INV>
 __device__ __forceinline__ void dif_mid(uint32_t* sm, const uint32_t* __restrict__ tw2) {
@@ -213,6 +246,31 @@ template <class S, int WT, int NT, bool INV, class Store>
 // others are neither computed nor stored.
 __device__ __forceinline__ void dif_last(uint32_t* sm, Store& store) {
   dif_last_sel<S, WT, NT, INV, false>(sm, store);
+}
+
+// Last DIF pass writing back into the slots: spectrum index j (slot b*R +
+// bitrev(q)) reduced to [0, p) when j < k, and zero otherwise (LOWER: k = L/2,
+// the even registers; the odd ones are not computed).
+template <class S, int WT, int NT, bool INV, bool LOWER>
+__device__ __forceinline__ void dif_last_reduce(uint32_t* sm, int k) {
+  static_assert(S::NP >= 2, "");
+  using Y = Lay<S, WT>;
+  constexpr int R = S::RL, B = ilog2(R);
+  for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
+    const int c = t % WT, b = t / WT;
+    if (!dbg_in(b * Y::LAST_B + c + (R - 1) * WT, Y::WORDS)) continue;
+    uint32_t* base = sm + b * Y::LAST_B + c;
+    uint32_t x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = base[q * WT];
+    dft_reg<R, INV>(x);
+    const int j0 = S::natural(b * R);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const bool keep = LOWER ? (q & 1) == 0 : j0 + (S::L / R) * bitrev(q, B) < k;
+      base[bitrev(q, B) * WT] = keep ? m_to_p(x[q]) : 0u;
+    }
+  }
 }
 
 // Last DIF pass writing back into the slots (for a following DIT sequence).

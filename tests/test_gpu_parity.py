@@ -183,6 +183,33 @@ def test_decode_full_and_half_width_tiles(pkg, n, k, W):
     assert np.array_equal(got[:, cols], want)
 
 
+@pytest.mark.parametrize("n,k,W,col,extra", [(8192, 4096, 96, 1, 3), (8192, 4096, 64, 4, 4),
+                                               (4096, 2048, 72, 2, 6), (8192, 3000, 40, 3, 5),
+                                               (1024, 512, 100, 0, 1)])
+def test_decode_output_leading_dimensions(pkg, n, k, W, col, extra):
+    # the staged decode writes a row's tile columns with one wide store when
+    # the row segment is aligned: an output inside a wider matrix, at an odd
+    # column or with an odd row length, takes the narrow stores instead
+    src = synth.source(13 * n + col, k, W)
+    plan = pkg.Plan(n, k)
+    enc = pkg.to_host(plan.encode(pkg.to_device(src)))
+    pos = synth.received_positions(n, synth.erased_uniform(n + col, n, k))
+    d_recv = pkg.to_device(np.ascontiguousarray(enc[pos]))
+    wide = torch.zeros((k, W + col + extra), dtype=torch.int16, device="cuda")
+    pkg.fnt_rs_decode(plan.handle, d_recv, pos, wide[:, col:col + W])
+    got = pkg.to_host(wide)
+    assert np.array_equal(got[:, col:col + W], src)
+    assert not got[:, :col].any() and not got[:, col + W:].any()
+    assert plan.status() == 0
+    v = synth.received_uniform(W + col, k, W)
+    wide.zero_()
+    pkg.fnt_rs_decode(plan.handle, pkg.to_device(v), pos, wide[:, col:col + W])
+    got = pkg.to_host(wide)[:, col:col + W]
+    cols = [0, 1, W // 2, W - 2, W - 1]
+    want, _ = oracle.decode(np.ascontiguousarray(v[:, cols]), pos, n, k)
+    assert np.array_equal(got[:, cols], want)
+
+
 @pytest.mark.parametrize("n,k,W", [(16384, 8192, 8), (16384, 12000, 5), (65536, 32768, 3),
                                    (32768, 30000, 3), (32768, 16384, 4), (32768, 10000, 3)])
 def test_decode_split_sizes_sampled(pkg, n, k, W):
