@@ -207,7 +207,8 @@ int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st)
         cudaSuccess)
       return -1;
     int o = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, max_smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT + 32, max_smem) !=
+        cudaSuccess)
       o = 1;
     occ[dev & 63] = o > 0 ? o : 1;
     done[dev & 63] = true;
@@ -215,7 +216,8 @@ int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st)
   const int nwide = (a.W + WT - 1) / WT;
   const int nfull = tail_full_tiles(nwide, t.sms * occ[dev & 63], WT);
   const int grid = nfull + 2 * (nwide - nfull);  // one CTA per tile (see clc_take)
-  kern<<<grid, NT, smem, st>>>(a, t.rowtab, t.rows_staged, t.box_rows, nfull,
+  // NT decoding threads and one producer warp
+  kern<<<grid, NT + 32, smem, st>>>(a, t.rowtab, t.rows_staged, t.box_rows, nfull,
                                *static_cast<const CUtensorMap*>(t.map));
   count_launch();
   return 0;

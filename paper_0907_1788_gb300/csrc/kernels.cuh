@@ -905,7 +905,7 @@ struct LoadStaged {
 // HALF (k = n/2 exactly): the truncation keeps the even registers of the
 // last D1 pass, so the first D2 pass sees a zero upper half, and D3 stores
 // only j < n/2; the compiler drops the butterfly halves nobody reads.
-template <class S, int WT, int NT, bool HALF>
+template <class S, int WT, int NT, bool HALF, class Sync = CtaSync>
 __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) {
   using Y = Lay<S, WT>;
   const uint32_t* tw1f = a.twf;
@@ -913,7 +913,7 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
   const uint32_t* __restrict__ ahat = a.ahat;
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
-    mid_last_sync<S, WT, NT>();  // the last pass reads only its group's blocks
+    mid_last_sync<S, WT, NT, Sync>();  // the last pass reads only its group's blocks
   }
   // last D1 pass + truncation to j < k + first D2 pass (DIT, root r)
   {
@@ -943,11 +943,11 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
     }
   }
   if constexpr (S::NP == 3) {
-    mid_last_sync<S, WT, NT>();
+    mid_last_sync<S, WT, NT, Sync>();
     dit_mid<S, WT, NT, false>(sm, tw1f + S::TW2_OFF);
-    __syncthreads();
+    Sync::sync();
   } else {
-    __syncthreads();
+    Sync::sync();
   }
   // last D2 pass * ahat + first D3 pass
   {
@@ -970,10 +970,10 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
       for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
     }
   }
-  __syncthreads();
+  Sync::sync();
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
-    mid_last_sync<S, WT, NT>();
+    mid_last_sync<S, WT, NT, Sync>();
   }
 }
 
@@ -1059,19 +1059,19 @@ __device__ __forceinline__ void copy_out(uint32_t* sm, StoreOut16<WT>& store, in
 // barrier) as soon as the scatter has read the stage; the first D1 pass then
 // works in place, and the last D3 pass writes back reduced values for
 // copy_out, which leaves the buffer zero again.
-template <class S, int WT, int NT, bool HALF, class F>
+template <class S, int WT, int NT, bool HALF, class Sync, class F>
 __device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t* stage, int sw,
                                                     const uint32_t* __restrict__ rowtab,
                                                     uint32_t& vmax, StoreOut16<WT>& store,
                                                     const KArgs& a, F&& freed) {
   scatter_received<S, WT, NT>(sm, stage, sw, rowtab, a.k, vmax);
-  __syncthreads();
+  Sync::sync();
   freed();
   dif_first_inplace<S, WT, NT, true>(sm, a.twi);
-  __syncthreads();
-  decode_mid_passes<S, WT, NT, HALF>(sm, a);
+  Sync::sync();
+  decode_mid_passes<S, WT, NT, HALF, Sync>(sm, a);
   dif_last_reduce<S, WT, NT, true, HALF>(sm, a.k);
-  __syncthreads();
+  Sync::sync();
   copy_out<S, WT, NT, HALF>(sm, store, a.k);
 }
 
@@ -1080,22 +1080,33 @@ __device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t
 // last round of tiles, which would otherwise keep only part of the SMs busy,
 // is spread over twice as many CTAs.  With nfull = ceil(W / WT) every tile is
 // WT wide.
+//
+// Roles: the first NT threads decode; one more warp (its lane 0) is the
+// producer, which takes over tiles of CTAs not yet launched and issues their
+// TMA loads.  Issuing a stage takes the producer a few thousand cycles (the
+// TMA unit accepts a box only as fast as it works through the box's 16-byte
+// rows), time the decoding warps would otherwise spend waiting for it at
+// their next barrier.  Hand-over, per tile: `bar` completes when the stage
+// has landed (s_tile, written before the producer's arrival, names the tile;
+// ntiles: none left), `ebar` when the decoding warps have read the stage.
 template <class S, int WT, int NT, bool HALF>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT + 32, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ rowtab, int rows_staged, int box_rows,
                  int nfull, const __grid_constant__ CUtensorMap trecv) {
   static_assert(S::NP >= 2, "");
   dbg_enter(a.status);
   using Y = Lay<S, WT>;
+  using Sync = FirstSync<NT>;
   constexpr int WH = WT >= 2 ? WT / 2 : 1;
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
   extern __shared__ __align__(128) uint4 smem_raw[];
-  __shared__ int s_next;
+  __shared__ int s_tile;
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)rows_staged * WT);
   uint64_t* cbar = bar + 1;
-  uint4* resp = reinterpret_cast<uint4*>(bar + 2);
+  uint64_t* ebar = bar + 2;
+  uint4* resp = reinterpret_cast<uint4*>(bar + 4);
   const int nwide = (a.W + WT - 1) / WT;
   if (WT < 2 || nfull > nwide) nfull = nwide;
   const int ntiles = nfull + 2 * (nwide - nfull);
@@ -1103,72 +1114,92 @@ __global__ void __launch_bounds__(NT, 1)
   auto box_x = [&](int t) { return t < nfull ? t * WT : (nfull + ((t - nfull) >> 1)) * WT; };
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
-  int tile = blockIdx.x;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
+    mbar_init(ebar, 1);
   }
   // the work buffer starts all zero (decode_scatter_tile keeps it so)
-  for (int i = threadIdx.x; i < WORK_BYTES / 16; i += NT) smem_raw[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = threadIdx.x; i < WORK_BYTES / 16; i += NT + 32)
+    smem_raw[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  if (threadIdx.x == 0 && tile < ntiles) {
-    mbar_expect_tx(bar, tx_bytes);
-    for (int bx = 0; bx < nbox; ++bx)
-      tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(tile), bx * box_rows, bar);
-    clc_request(resp, cbar);
+
+  if (threadIdx.x >= NT) {
+    // ---- producer (one thread)
+    if (threadIdx.x != NT) return;
+    auto issue = [&](int t) {
+      s_tile = t;
+      mbar_expect_tx(bar, tx_bytes);  // this thread's arrival, plus the stage's bytes
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(t), bx * box_rows, bar);
+    };
+    int tile = blockIdx.x;
+    uint32_t ephase = 0, cphase = 0, fphase = 0;
+    if (tile < ntiles) {
+      issue(tile);
+      clc_request(resp, cbar);
+    } else {
+      s_tile = ntiles;
+      mbar_arrive(bar);
+      return;
+    }
+    while (tile < ntiles) {
+      // the decoding warps have read the stage of `tile`
+      if (!mbar_wait(ebar, ephase)) {
+        atomicOr(a.status, ST_TIMEOUT);
+        mbar_wait(bar, fphase);  // let the copy in flight land
+        mbar_wait(cbar, cphase);
+        return;
+      }
+      ephase ^= 1u;
+      fphase ^= 1u;
+      int nxt = clc_take(resp, cbar, cphase);
+      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
+      if (nxt >= 0 && nxt < ntiles) {
+        fence_proxy_async();
+        issue(nxt);
+        clc_request(resp, cbar);
+      } else {
+        nxt = ntiles;
+        s_tile = ntiles;
+        mbar_arrive(bar);  // no bytes: the phase completes, the decoding warps stop
+      }
+      tile = nxt;
+    }
+    return;
   }
-  uint32_t parity = 0, cphase = 0;
-  bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
+
+  // ---- decoding warps
+  uint32_t parity = 0;
   uint32_t vmax = 0u;  // largest received value seen (> 65536 is out of range)
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
   auto freed = [&]() {
-    if (threadIdx.x == 0) {
-      // the stage is free: take over a pending CTA's tile and prefetch it
-      int nxt = clc_take(resp, cbar, cphase);
-      pending = false;
-      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
-      if (nxt >= 0 && nxt < ntiles) {
-        fence_proxy_async();
-        mbar_expect_tx(bar, tx_bytes);
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(nxt), bx * box_rows,
-                      bar);
-        clc_request(resp, cbar);
-        pending = true;
-      } else {
-        nxt = ntiles;
-      }
-      s_next = nxt;
-    }
+    if (threadIdx.x == 0) mbar_arrive(ebar);  // the stage is free for the producer
   };
-  while (tile < ntiles) {
+  for (;;) {
     const bool ok = mbar_wait(bar, parity);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicOr(a.status, ST_TIMEOUT);
-        mbar_wait(bar, parity);  // let the copy in flight land before exiting
-        if (pending) mbar_wait(cbar, cphase);
-      }
+    if (first_sync_or<NT>(!ok)) {
+      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
       return;
     }
     parity ^= 1u;
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
     if constexpr (WT >= 2) {
       if (tile >= nfull) {
         // a half tile: columns (tile - nfull) & 1 of its box, WH codewords
         const int h = tile - nfull;
         store_h.col0 = nfull * WT + h * WH;
-        decode_scatter_tile<S, WH, NT, HALF>(sm, stage + (h & 1) * WH, WT, rowtab, vmax, store_h,
-                                             a, freed);
-        __syncthreads();
-        tile = s_next;
+        decode_scatter_tile<S, WH, NT, HALF, Sync>(sm, stage + (h & 1) * WH, WT, rowtab, vmax,
+                                                   store_h, a, freed);
+        Sync::sync();
         continue;
       }
     }
     store.col0 = tile * WT;
-    decode_scatter_tile<S, WT, NT, HALF>(sm, stage, WT, rowtab, vmax, store, a, freed);
-    __syncthreads();
-    tile = s_next;
+    decode_scatter_tile<S, WT, NT, HALF, Sync>(sm, stage, WT, rowtab, vmax, store, a, freed);
+    Sync::sync();
   }
   if (vmax > 65536u) atomicOr(a.status, ST_RANGE);
   store.flush();

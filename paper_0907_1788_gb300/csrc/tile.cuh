@@ -112,6 +112,20 @@ __device__ __forceinline__ void bitrev_regs(uint32_t* x) {
   for (int j = 0; j < R; ++j) x[j] = y[j];
 }
 
+// CTA-wide barriers of the pass sequences: every thread of the CTA, or only
+// the first N (named barrier 15), when the CTA has other warps (a TMA
+// producer) that never take part.
+struct CtaSync {
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+template <int N>
+struct FirstSync {
+  static_assert(N % 32 == 0, "");
+  static __device__ __forceinline__ void sync() {
+    asm volatile("bar.sync 15, %0;" ::"n"(N) : "memory");
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Barrier between the middle pass and the last pass of a 3-pass schedule (in
 // either direction).  With R2 = RL both passes give the S1 slots of one middle
@@ -119,14 +133,14 @@ __device__ __forceinline__ void bitrev_regs(uint32_t* x) {
 // thread t mod NT; when G is a multiple of the warp size that divides NT, the
 // threads that write a block are the threads that read it, so only their
 // group of G threads (thread index / G) has to meet: one warp (syncwarp) or a
-// named barrier of G threads (ids 1..NT/G; id 0 is __syncthreads).  Otherwise
-// the whole CTA meets.
+// named barrier of G threads (ids 1..NT/G; id 0 is __syncthreads, 15 FirstSync).  Otherwise
+// the whole CTA (Sync) meets.
 // ---------------------------------------------------------------------------
-template <class S, int WT, int NT>
+template <class S, int WT, int NT, class Sync = CtaSync>
 __device__ __forceinline__ void mid_last_sync() {
   constexpr int G = (S::NP == 3) ? (S::S1 / S::R2) * WT : 0;
   if constexpr (S::NP == 3 && S::R2 == S::RL && G % 32 == 0 && G > 0 && NT % G == 0 &&
-                NT / G <= 15) {
+                NT / G <= 14) {  // ids 1..14 (15: FirstSync)
     if constexpr (G == 32) {
       __syncwarp();
     } else {
@@ -134,7 +148,7 @@ __device__ __forceinline__ void mid_last_sync() {
       asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(G) : "memory");
     }
   } else {
-    __syncthreads();
+    Sync::sync();
   }
 }
 

@@ -27,6 +27,27 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// one arrival without transaction bytes (release: this thread's earlier
+// shared-memory writes are seen by whoever completes a wait on the phase)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// OR of `v` over the first N threads of the CTA (named barrier 15, as FirstSync)
+template <int N>
+__device__ __forceinline__ bool first_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 15, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(N)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -111,7 +132,8 @@ __device__ __forceinline__ int clc_take(const uint4* resp, uint64_t* bar, uint32
 }
 
 // Shared-memory bytes after a TMA kernel's stage: the TMA barrier, the
-// cancel barrier and the 16-byte cancel response.
+// cancel barrier, (the decode's stage-empty barrier,) the 16-byte cancel
+// response at byte 32.
 constexpr int kSchedBytes = 64;
 
 }  // namespace fntrs
