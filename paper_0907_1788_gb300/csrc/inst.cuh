@@ -172,7 +172,7 @@ int launch_encode_tma_t(const KArgs& a, const uint32_t* twc, int rows_staged, in
       return -1;
     done[dev & 63] = true;
   }
-  kern<<<grid, NT, smem, st>>>(a, twc, rows_staged, box_rows, map);
+  kern<<<grid, NT + 32, smem, st>>>(a, twc, rows_staged, box_rows, map);  // + producer warp
   count_launch();
   return 0;
 }

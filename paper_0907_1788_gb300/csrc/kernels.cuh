@@ -368,6 +368,72 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Stage hand-over of the one-stage TMA kernels (k_encode_tma, k_decode_tma):
+// one producer thread takes over tiles of CTAs not yet launched (cluster
+// launch control) and issues each tile's stage loads; the transforming
+// threads never wait for that issue.  Issuing a stage takes the producer a
+// few thousand cycles (the TMA unit accepts a box only as fast as it works
+// through the box's 16-byte rows), time the transforming threads would
+// otherwise spend waiting for it at their next barrier.
+// kSchedBytes at `bar`: [0] full (the stage has landed; *s_tile, written
+// before the producer's arrival, names its tile, ntiles none), [1] cancel
+// response barrier, [2] empty (the transforming threads have read the
+// stage: `arrivals` arrivals), the 16-byte cancel response at byte 32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t* tma_empty_bar(uint64_t* bar) { return bar + 2; }
+
+__device__ __forceinline__ void tma_producer_init(uint64_t* bar, uint32_t arrivals = 1) {
+  mbar_init(bar, 1);
+  mbar_init(bar + 1, 1);
+  mbar_init(bar + 2, arrivals);
+}
+
+// issue(t): the loads of tile t's stage, completing on bar[0]
+template <class Issue>
+__device__ __forceinline__ void tma_producer(uint64_t* bar, int* s_tile, int* status, int ntiles,
+                                             uint32_t tx_bytes, Issue&& issue) {
+  uint64_t* cbar = bar + 1;
+  uint64_t* ebar = bar + 2;
+  uint4* resp = reinterpret_cast<uint4*>(bar + 4);
+  auto start = [&](int t) {
+    *s_tile = t;
+    mbar_expect_tx(bar, tx_bytes);  // this thread's arrival, plus the stage's bytes
+    issue(t);
+  };
+  int tile = blockIdx.x;
+  if (tile >= ntiles) {
+    *s_tile = ntiles;
+    mbar_arrive(bar);
+    return;
+  }
+  start(tile);
+  clc_request(resp, cbar);
+  uint32_t ephase = 0, cphase = 0, fphase = 0;
+  while (tile < ntiles) {
+    if (!mbar_wait(ebar, ephase)) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait(bar, fphase);  // let the copy in flight land
+      mbar_wait(cbar, cphase);
+      return;
+    }
+    ephase ^= 1u;
+    fphase ^= 1u;
+    int nxt = clc_take(resp, cbar, cphase);
+    if (nxt == kClcTimeout) atomicOr(status, ST_TIMEOUT);
+    if (nxt >= 0 && nxt < ntiles) {
+      fence_proxy_async();
+      start(nxt);
+      clc_request(resp, cbar);
+    } else {
+      nxt = ntiles;
+      *s_tile = ntiles;
+      mbar_arrive(bar);  // no bytes: the phase completes and the transforming threads stop
+    }
+    tile = nxt;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Encode with TMA-staged source (n = C * L, C in {1, 2}, k <= L).  One CTA
 // per column tile of WT codewords; a running CTA takes over tiles of CTAs not
 // yet launched (cluster launch control, see clc_take), and the [k][WT] source
@@ -379,14 +445,17 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
 // smem: work (Lay WORDS u32) | stage (rows_staged * WT u16) | barriers and
 // cancel response (kSchedBytes).
 // ---------------------------------------------------------------------------
+// Roles as in k_decode_tma: NT threads transform, one more warp (its lane 0)
+// takes over tiles and issues their stage loads (tma_producer).
 template <class S, int WT, int NT, int C>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT + 32, 1)
     k_encode_tma(KArgs a, const uint32_t* __restrict__ twc, int rows_staged, int box_rows,
                  const __grid_constant__ CUtensorMap tsrc) {
   static_assert(S::NP == 3 || S::NP == 2, "");
   static_assert(C == 1 || (C == 2 && 2 * S::R1 <= 32), "");
   dbg_enter(a.status);
   using Y = Lay<S, WT>;
+  using Sync = FirstSync<NT>;
   constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
   constexpr int WORK_BYTES = ((Y::WORDS * 4) + 127) / 128 * 128;
   extern __shared__ __align__(128) uint4 smem_raw[];
@@ -394,39 +463,32 @@ __global__ void __launch_bounds__(NT, 1)
   uint16_t* stage = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(stage) +
                                               (size_t)rows_staged * WT * 2);
-  uint64_t* cbar = bar + 1;
-  uint4* resp = reinterpret_cast<uint4*>(bar + 2);
-  __shared__ int s_next;
+  __shared__ int s_tile;
   const int ntiles = (a.W + WT - 1) / WT;
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 2;
-  int tile = blockIdx.x;
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    mbar_init(cbar, 1);
-  }
+  if (threadIdx.x == 0) tma_producer_init(bar);
   __syncthreads();
-  if (threadIdx.x == 0 && tile < ntiles) {
-    mbar_expect_tx(bar, tx_bytes);
-    for (int bx = 0; bx < nbox; ++bx)
-      tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, tile * WT, bx * box_rows, bar);
-    clc_request(resp, cbar);
+  if (threadIdx.x >= NT) {
+    if (threadIdx.x == NT)
+      tma_producer(bar, &s_tile, a.status, ntiles, tx_bytes, [&](int t) {
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, t * WT, bx * box_rows, bar);
+      });
+    return;
   }
-  uint32_t parity = 0, cphase = 0;
-  bool pending = tile < ntiles;  // thread 0: a cancel request is outstanding
+  uint32_t parity = 0;
   uint32_t* out = static_cast<uint32_t*>(a.out);
   const size_t ld = a.ld_out;
-  while (tile < ntiles) {
+  for (;;) {
     const bool ok = mbar_wait(bar, parity);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicOr(a.status, ST_TIMEOUT);
-        mbar_wait(bar, parity);  // let the copy in flight land before exiting
-        if (pending) mbar_wait(cbar, cphase);
-      }
+    if (first_sync_or<NT>(!ok)) {
+      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
       return;
     }
     parity ^= 1u;
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
     const int col0 = tile * WT;
 #pragma unroll 1
     for (int cc = 0; cc < C; ++cc) {
@@ -462,27 +524,12 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int q = 0; q < R; ++q) base[bitrev(q, B) * Y::P1_STRIDE] = x[q];
       }
-      __syncthreads();
-      if (cc == C - 1 && threadIdx.x == 0) {
-        // the stage is free: take over a pending CTA's tile and prefetch it
-        int nxt = clc_take(resp, cbar, cphase);
-        pending = false;
-        if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
-        if (nxt >= 0 && nxt < ntiles) {
-          fence_proxy_async();
-          mbar_expect_tx(bar, tx_bytes);
-          for (int bx = 0; bx < nbox; ++bx)
-            tma_load_2d(stage + (size_t)bx * box_rows * WT, &tsrc, nxt * WT, bx * box_rows, bar);
-          clc_request(resp, cbar);
-          pending = true;
-        } else {
-          nxt = ntiles;
-        }
-        s_next = nxt;
-      }
+      Sync::sync();
+      // the stage is free for the producer once the last class has read it
+      if (cc == C - 1 && threadIdx.x == 0) mbar_arrive(tma_empty_bar(bar));
       if constexpr (S::NP == 3) {
         dif_mid<S, WT, NT, false>(work, a.twf + S::TW2_OFF);
-        mid_last_sync<S, WT, NT>();  // the last pass reads only its group's blocks
+        mid_last_sync<S, WT, NT, Sync>();  // the last pass reads only its group's blocks
       }
       // last pass -> encoded rows cc + C*j
       {
@@ -528,9 +575,8 @@ __global__ void __launch_bounds__(NT, 1)
           }
         }
       }
-      __syncthreads();
+      Sync::sync();
     }
-    tile = s_next;
   }
 }
 
@@ -1081,14 +1127,8 @@ __device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t
 // is spread over twice as many CTAs.  With nfull = ceil(W / WT) every tile is
 // WT wide.
 //
-// Roles: the first NT threads decode; one more warp (its lane 0) is the
-// producer, which takes over tiles of CTAs not yet launched and issues their
-// TMA loads.  Issuing a stage takes the producer a few thousand cycles (the
-// TMA unit accepts a box only as fast as it works through the box's 16-byte
-// rows), time the decoding warps would otherwise spend waiting for it at
-// their next barrier.  Hand-over, per tile: `bar` completes when the stage
-// has landed (s_tile, written before the producer's arrival, names the tile;
-// ntiles: none left), `ebar` when the decoding warps have read the stage.
+// Roles: the first NT threads decode; one more warp (its lane 0) takes over
+// tiles and issues their stage loads (tma_producer).
 template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT + 32, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ rowtab, int rows_staged, int box_rows,
@@ -1104,9 +1144,6 @@ __global__ void __launch_bounds__(NT + 32, 1)
   uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_raw) + WORK_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(stage + (size_t)rows_staged * WT);
-  uint64_t* cbar = bar + 1;
-  uint64_t* ebar = bar + 2;
-  uint4* resp = reinterpret_cast<uint4*>(bar + 4);
   const int nwide = (a.W + WT - 1) / WT;
   if (WT < 2 || nfull > nwide) nfull = nwide;
   const int ntiles = nfull + 2 * (nwide - nfull);
@@ -1114,58 +1151,17 @@ __global__ void __launch_bounds__(NT + 32, 1)
   auto box_x = [&](int t) { return t < nfull ? t * WT : (nfull + ((t - nfull) >> 1)) * WT; };
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    mbar_init(cbar, 1);
-    mbar_init(ebar, 1);
-  }
+  if (threadIdx.x == 0) tma_producer_init(bar);
   // the work buffer starts all zero (decode_scatter_tile keeps it so)
   for (int i = threadIdx.x; i < WORK_BYTES / 16; i += NT + 32)
     smem_raw[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-
   if (threadIdx.x >= NT) {
-    // ---- producer (one thread)
-    if (threadIdx.x != NT) return;
-    auto issue = [&](int t) {
-      s_tile = t;
-      mbar_expect_tx(bar, tx_bytes);  // this thread's arrival, plus the stage's bytes
-      for (int bx = 0; bx < nbox; ++bx)
-        tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(t), bx * box_rows, bar);
-    };
-    int tile = blockIdx.x;
-    uint32_t ephase = 0, cphase = 0, fphase = 0;
-    if (tile < ntiles) {
-      issue(tile);
-      clc_request(resp, cbar);
-    } else {
-      s_tile = ntiles;
-      mbar_arrive(bar);
-      return;
-    }
-    while (tile < ntiles) {
-      // the decoding warps have read the stage of `tile`
-      if (!mbar_wait(ebar, ephase)) {
-        atomicOr(a.status, ST_TIMEOUT);
-        mbar_wait(bar, fphase);  // let the copy in flight land
-        mbar_wait(cbar, cphase);
-        return;
-      }
-      ephase ^= 1u;
-      fphase ^= 1u;
-      int nxt = clc_take(resp, cbar, cphase);
-      if (nxt == kClcTimeout) atomicOr(a.status, ST_TIMEOUT);
-      if (nxt >= 0 && nxt < ntiles) {
-        fence_proxy_async();
-        issue(nxt);
-        clc_request(resp, cbar);
-      } else {
-        nxt = ntiles;
-        s_tile = ntiles;
-        mbar_arrive(bar);  // no bytes: the phase completes, the decoding warps stop
-      }
-      tile = nxt;
-    }
+    if (threadIdx.x == NT)
+      tma_producer(bar, &s_tile, a.status, ntiles, tx_bytes, [&](int t) {
+        for (int bx = 0; bx < nbox; ++bx)
+          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(t), bx * box_rows, bar);
+      });
     return;
   }
 
@@ -1175,7 +1171,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
   StoreOut16<WT> store = StoreOut16<WT>::make(a, 0, 0);
   StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
   auto freed = [&]() {
-    if (threadIdx.x == 0) mbar_arrive(ebar);  // the stage is free for the producer
+    if (threadIdx.x == 0) mbar_arrive(tma_empty_bar(bar));  // the stage is free for the producer
   };
   for (;;) {
     const bool ok = mbar_wait(bar, parity);
