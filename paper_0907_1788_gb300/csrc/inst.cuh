@@ -195,6 +195,9 @@ inline int tail_full_tiles(int nwide, int resident, int wt) {
 template <class S, int WT, int NT, bool HALF>
 int launch_decode_tma_h(const KArgs& a, const TmaDecodeArgs& t, cudaStream_t st) {
   auto kern = k_decode_tma<S, WT, NT, HALF>;
+  // the staged tables (HALF, L >= 4096) need the stage to hold 2 L words
+  if (HALF && S::L >= 4096 && (!a.twf_sw || (size_t)t.rows_staged * WT < 2 * (size_t)S::L))
+    return -1;
   constexpr int work = ((Lay<S, WT>::WORDS * 4) + 127) / 128 * 128;
   const int smem = work + t.rows_staged * WT * 4 + kSchedBytes;
   static bool done[64] = {};

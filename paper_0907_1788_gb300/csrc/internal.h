@@ -16,6 +16,7 @@ namespace fntrs {
 struct Tables {
   uint32_t* twf = nullptr;
   uint32_t* twi = nullptr;
+  uint32_t* twf_sw = nullptr;  // pass-1 part of twf, 16-byte chunks of row i2 rotated (decode_tw_sw)
   uint32_t* powf = nullptr;
   uint32_t* powi = nullptr;
 };

@@ -48,6 +48,7 @@ struct KArgs {
   uint32_t scale = 1;
   const uint32_t* twf = nullptr;   // per-pass tables of the L-schedule, forward root
   const uint32_t* twi = nullptr;   // same, inverse root
+  const uint32_t* twf_sw = nullptr;  // pass-1 part of twf, chunks swizzled per row (or null)
   const uint32_t* powf = nullptr;  // r_n^e, e < n
   const uint32_t* powi = nullptr;  // r_n^-e, e < n
   const uint2* pat = nullptr;      // decode gather table, one {row, weight} per position

@@ -378,20 +378,28 @@ __global__ void __launch_bounds__(NT) k_tile(KArgs a) {
 // kSchedBytes at `bar`: [0] full (the stage has landed; *s_tile, written
 // before the producer's arrival, names its tile, ntiles none), [1] cancel
 // response barrier, [2] empty (the transforming threads have read the
-// stage: `arrivals` arrivals), the 16-byte cancel response at byte 32.
+// stage: `arrivals` arrivals), [3] tables (TABLES below), the 16-byte cancel
+// response at byte 32.
+// TABLES: between two tiles the stage also carries tables for a later pass:
+// once the stage has been read, tables() copies them in (completing
+// table_bytes on bar[3]), and the next tile is loaded after a second arrival
+// on bar[2] (the tables have been read).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t* tma_empty_bar(uint64_t* bar) { return bar + 2; }
+__device__ __forceinline__ uint64_t* tma_tables_bar(uint64_t* bar) { return bar + 3; }
 
 __device__ __forceinline__ void tma_producer_init(uint64_t* bar, uint32_t arrivals = 1) {
   mbar_init(bar, 1);
   mbar_init(bar + 1, 1);
   mbar_init(bar + 2, arrivals);
+  mbar_init(bar + 3, 1);
 }
 
 // issue(t): the loads of tile t's stage, completing on bar[0]
-template <class Issue>
+template <bool TABLES = false, class Issue, class Tables = int>
 __device__ __forceinline__ void tma_producer(uint64_t* bar, int* s_tile, int* status, int ntiles,
-                                             uint32_t tx_bytes, Issue&& issue) {
+                                             uint32_t tx_bytes, Issue&& issue,
+                                             Tables&& tables = 0, uint32_t table_bytes = 0) {
   uint64_t* cbar = bar + 1;
   uint64_t* ebar = bar + 2;
   uint4* resp = reinterpret_cast<uint4*>(bar + 4);
@@ -408,7 +416,7 @@ __device__ __forceinline__ void tma_producer(uint64_t* bar, int* s_tile, int* st
   }
   start(tile);
   clc_request(resp, cbar);
-  uint32_t ephase = 0, cphase = 0, fphase = 0;
+  uint32_t ephase = 0, cphase = 0, fphase = 0, tphase = 0;
   while (tile < ntiles) {
     if (!mbar_wait(ebar, ephase)) {
       atomicOr(status, ST_TIMEOUT);
@@ -418,6 +426,19 @@ __device__ __forceinline__ void tma_producer(uint64_t* bar, int* s_tile, int* st
     }
     ephase ^= 1u;
     fphase ^= 1u;
+    if constexpr (TABLES) {
+      fence_proxy_async();
+      mbar_expect_tx(bar + 3, table_bytes);
+      tables();
+      if (!mbar_wait(ebar, ephase)) {
+        atomicOr(status, ST_TIMEOUT);
+        mbar_wait(bar + 3, tphase);  // let the copies in flight land
+        mbar_wait(cbar, cphase);
+        return;
+      }
+      ephase ^= 1u;
+      tphase ^= 1u;
+    }
     int nxt = clc_take(resp, cbar, cphase);
     if (nxt == kClcTimeout) atomicOr(status, ST_TIMEOUT);
     if (nxt >= 0 && nxt < ntiles) {
@@ -951,8 +972,14 @@ struct LoadStaged {
 // HALF (k = n/2 exactly): the truncation keeps the even registers of the
 // last D1 pass, so the first D2 pass sees a zero upper half, and D3 stores
 // only j < n/2; the compiler drops the butterfly halves nobody reads.
-template <class S, int WT, int NT, bool HALF, class Sync = CtaSync>
-__device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) {
+// TS: the pass that multiplies by ahat reads its forward twiddles and ahat
+// from shared memory, tws = [pass-1 twiddles, chunks permuted (twf_sw) | ahat]
+// (L words each); hook(0) runs before that pass (in every thread: the tables
+// have landed), hook(1) after the barrier that ends it (they may be
+// overwritten).
+template <class S, int WT, int NT, bool HALF, class Sync, bool TS, class H>
+__device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a,
+                                                  const uint32_t* tws, H&& hook) {
   using Y = Lay<S, WT>;
   const uint32_t* tw1f = a.twf;
   const uint32_t* tw1i = a.twi;
@@ -996,6 +1023,7 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
     Sync::sync();
   }
   // last D2 pass * ahat + first D3 pass
+  if constexpr (TS) hook(0);
   {
     constexpr int R = S::R1, SP = S::S1, B = ilog2(R);
     for (int t = threadIdx.x; t < (S::L / R) * WT; t += NT) {
@@ -1004,11 +1032,17 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
       uint32_t x[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) x[q] = base[bitrev(q, B) * Y::P1_STRIDE];
-      twiddle_regs<R>(x, tw1f + i2 * R);
+      if constexpr (TS)
+        twiddle_regs_sw<R>(x, tws + i2 * R, i2);
+      else
+        twiddle_regs<R>(x, tw1f + i2 * R);
       bitrev_regs<R>(x);
       dft_reg<R, false>(x);
 #pragma unroll
-      for (int q = 0; q < R; ++q) x[q] = m_mul(x[q], __ldg(ahat + bitrev(q, B) * SP + i2));
+      for (int q = 0; q < R; ++q) {
+        const int i = bitrev(q, B) * SP + i2;
+        x[q] = m_mul(x[q], TS ? tws[S::L + i] : __ldg(ahat + i));
+      }
       bitrev_regs<R>(x);
       dft_reg<R, true>(x);
       twiddle_regs<R>(x, tw1i + i2 * R);
@@ -1017,6 +1051,7 @@ __device__ __forceinline__ void decode_mid_passes(uint32_t* sm, const KArgs& a) 
     }
   }
   Sync::sync();
+  if constexpr (TS) hook(1);
   if constexpr (S::NP == 3) {
     dif_mid<S, WT, NT, true>(sm, tw1i + S::TW2_OFF);
     mid_last_sync<S, WT, NT, Sync>();
@@ -1034,7 +1069,7 @@ __device__ __forceinline__ void decode_staged_tile(uint32_t* sm, LD& load, ST& s
   dif_first<S, WT, NT, true>(sm, a.twi, load, nop);
   __syncthreads();
   freed();
-  decode_mid_passes<S, WT, NT, HALF>(sm, a);
+  decode_mid_passes<S, WT, NT, HALF, CtaSync, false>(sm, a, nullptr, [](int) {});
   dif_last_sel<S, WT, NT, true, HALF>(sm, store);
 }
 
@@ -1105,17 +1140,18 @@ __device__ __forceinline__ void copy_out(uint32_t* sm, StoreOut16<WT>& store, in
 // barrier) as soon as the scatter has read the stage; the first D1 pass then
 // works in place, and the last D3 pass writes back reduced values for
 // copy_out, which leaves the buffer zero again.
-template <class S, int WT, int NT, bool HALF, class Sync, class F>
+template <class S, int WT, int NT, bool HALF, class Sync, bool TS, class F, class H>
 __device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t* stage, int sw,
                                                     const uint32_t* __restrict__ rowtab,
                                                     uint32_t& vmax, StoreOut16<WT>& store,
-                                                    const KArgs& a, F&& freed) {
+                                                    const KArgs& a, F&& freed,
+                                                    const uint32_t* tws, H&& hook) {
   scatter_received<S, WT, NT>(sm, stage, sw, rowtab, a.k, vmax);
   Sync::sync();
   freed();
   dif_first_inplace<S, WT, NT, true>(sm, a.twi);
   Sync::sync();
-  decode_mid_passes<S, WT, NT, HALF, Sync>(sm, a);
+  decode_mid_passes<S, WT, NT, HALF, Sync, TS>(sm, a, tws, hook);
   dif_last_reduce<S, WT, NT, true, HALF>(sm, a.k);
   Sync::sync();
   copy_out<S, WT, NT, HALF>(sm, store, a.k);
@@ -1129,6 +1165,11 @@ __device__ __forceinline__ void decode_scatter_tile(uint32_t* sm, const uint32_t
 //
 // Roles: the first NT threads decode; one more warp (its lane 0) takes over
 // tiles and issues their stage loads (tma_producer).
+// TS (k = n/2, L >= 4096, where the tables outgrow the L1 cache that the
+// 200 KB of shared memory leave): once a tile's received rows are scattered,
+// the producer copies the forward pass-1 twiddles (chunks permuted, twf_sw)
+// and ahat into the stage for the pass that multiplies by ahat, and loads the
+// next tile after that pass (the passes after it cover the load).
 template <class S, int WT, int NT, bool HALF>
 __global__ void __launch_bounds__(NT + 32, 1)
     k_decode_tma(KArgs a, const uint32_t* __restrict__ rowtab, int rows_staged, int box_rows,
@@ -1151,6 +1192,8 @@ __global__ void __launch_bounds__(NT + 32, 1)
   auto box_x = [&](int t) { return t < nfull ? t * WT : (nfull + ((t - nfull) >> 1)) * WT; };
   const int nbox = rows_staged / box_rows;
   const uint32_t tx_bytes = (uint32_t)rows_staged * WT * 4;
+  // (the launch guarantees rows_staged * WT >= 2 L and twf_sw set)
+  constexpr bool TS = HALF && S::L >= 4096;
   if (threadIdx.x == 0) tma_producer_init(bar);
   // the work buffer starts all zero (decode_scatter_tile keeps it so)
   for (int i = threadIdx.x; i < WORK_BYTES / 16; i += NT + 32)
@@ -1158,10 +1201,18 @@ __global__ void __launch_bounds__(NT + 32, 1)
   __syncthreads();
   if (threadIdx.x >= NT) {
     if (threadIdx.x == NT)
-      tma_producer(bar, &s_tile, a.status, ntiles, tx_bytes, [&](int t) {
-        for (int bx = 0; bx < nbox; ++bx)
-          tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(t), bx * box_rows, bar);
-      });
+      tma_producer<TS>(
+          bar, &s_tile, a.status, ntiles, tx_bytes,
+          [&](int t) {
+            for (int bx = 0; bx < nbox; ++bx)
+              tma_load_2d(stage + (size_t)bx * box_rows * WT, &trecv, box_x(t), bx * box_rows,
+                          bar);
+          },
+          [&]() {
+            bulk_load(stage, a.twf_sw, 4u * S::L, tma_tables_bar(bar));
+            bulk_load(stage + S::L, a.ahat, 4u * S::L, tma_tables_bar(bar));
+          },
+          8u * S::L);
     return;
   }
 
@@ -1172,6 +1223,15 @@ __global__ void __launch_bounds__(NT + 32, 1)
   StoreOut16<WH> store_h = StoreOut16<WH>::make(a, 0, 0);
   auto freed = [&]() {
     if (threadIdx.x == 0) mbar_arrive(tma_empty_bar(bar));  // the stage is free for the producer
+  };
+  uint32_t tpar = 0;
+  auto tables = [&](int ev) {
+    if (ev == 0) {
+      if (!mbar_wait(tma_tables_bar(bar), tpar)) atomicOr(a.status, ST_TIMEOUT);
+      tpar ^= 1u;
+    } else if (threadIdx.x == 0) {
+      mbar_arrive(tma_empty_bar(bar));  // the tables have been read
+    }
   };
   for (;;) {
     const bool ok = mbar_wait(bar, parity);
@@ -1187,14 +1247,15 @@ __global__ void __launch_bounds__(NT + 32, 1)
         // a half tile: columns (tile - nfull) & 1 of its box, WH codewords
         const int h = tile - nfull;
         store_h.col0 = nfull * WT + h * WH;
-        decode_scatter_tile<S, WH, NT, HALF, Sync>(sm, stage + (h & 1) * WH, WT, rowtab, vmax,
-                                                   store_h, a, freed);
+        decode_scatter_tile<S, WH, NT, HALF, Sync, TS>(sm, stage + (h & 1) * WH, WT, rowtab,
+                                                       vmax, store_h, a, freed, stage, tables);
         Sync::sync();
         continue;
       }
     }
     store.col0 = tile * WT;
-    decode_scatter_tile<S, WT, NT, HALF, Sync>(sm, stage, WT, rowtab, vmax, store, a, freed);
+    decode_scatter_tile<S, WT, NT, HALF, Sync, TS>(sm, stage, WT, rowtab, vmax, store, a, freed,
+                                                   stage, tables);
     Sync::sync();
   }
   if (vmax > 65536u) atomicOr(a.status, ST_RANGE);

@@ -172,6 +172,26 @@ static std::vector<uint32_t> sched_table(int L, bool inverse) {
   return out;
 }
 
+// The pass-1 part of the forward table (L entries, row i2 = the R1 entries of
+// task i2) with the 16-byte chunks of each row permuted: chunk u of row i2 at
+// chunk u ^ (i2 mod R1/4).  Copied into shared memory by the staged decode,
+// whose warps read chunk u of 32/WT consecutive rows at once: the permutation
+// puts those reads in different banks.
+static std::vector<uint32_t> sched_table_swizzled(int L) {
+  int r[3];
+  sched_radices(L, r);
+  const std::vector<uint32_t> t = sched_table(L, false);
+  std::vector<uint32_t> out;
+  const int R = r[0], S1 = L / R, nch = R / 4;
+  if (t.empty() || R < 4) return out;
+  out.resize(L);
+  for (int i2 = 0; i2 < S1; ++i2)
+    for (int u = 0; u < nch; ++u)
+      for (int e = 0; e < 4; ++e)
+        out[(size_t)i2 * R + 4 * (u ^ (i2 % nch)) + e] = t[(size_t)i2 * R + 4 * u + e];
+  return out;
+}
+
 static int upload(uint32_t** dst, const std::vector<uint32_t>& v) {
   const size_t bytes = std::max<size_t>(16, v.size() * sizeof(uint32_t));
   if (cudaMalloc(dst, bytes) != cudaSuccess) return FNT_RS_E_CUDA;
@@ -204,6 +224,7 @@ int get_tables(int L, Tables* out) {
   if (L <= kTileMaxL) {
     if ((rc = upload(&t.twf, sched_table(L, false))) || (rc = upload(&t.twi, sched_table(L, true))))
       return rc;
+    if (L >= 4096 && (rc = upload(&t.twf_sw, sched_table_swizzled(L)))) return rc;
   }
   g_tables[{dev, L}] = t;
   *out = t;
@@ -817,6 +838,7 @@ static int decode_tma(fnt_rs_plan_s* p, const PatternSlot& sl, const uint32_t* r
   a.C = 1;
   a.twf = p->tn.twf;
   a.twi = p->tn.twi;
+  a.twf_sw = p->tn.twf_sw;
   a.ahat = sl.ahat;
   a.status = p->status;
   a.out32 = out32;

@@ -101,6 +101,22 @@ __device__ __forceinline__ void twiddle_regs(uint32_t* x, const uint32_t* __rest
   }
 }
 
+// The same from a row of a table copied to shared memory with its 16-byte
+// chunks permuted (chunk u of row i2 at chunk u ^ (i2 mod R/4)).
+template <int R>
+__device__ __forceinline__ void twiddle_regs_sw(uint32_t* x, const uint32_t* row, int i2) {
+  static_assert(R >= 4, "");
+  const int m = i2 & (R / 4 - 1);
+#pragma unroll
+  for (int u = 0; u < R / 4; ++u) {
+    const uint4 w = reinterpret_cast<const uint4*>(row)[u ^ m];
+    if (u != 0) x[4 * u] = m_mul(x[4 * u], w.x);
+    x[4 * u + 1] = m_mul(x[4 * u + 1], w.y);
+    x[4 * u + 2] = m_mul(x[4 * u + 2], w.z);
+    x[4 * u + 3] = m_mul(x[4 * u + 3], w.w);
+  }
+}
+
 // x_nat[j] = x[bitrev(j)]  (DIF output order -> natural, or the reverse)
 template <int R>
 __device__ __forceinline__ void bitrev_regs(uint32_t* x) {
