@@ -297,7 +297,9 @@ def ragged_measure(pkg, dev, wave_bytes=32 << 30, nstreams=16, max_groups=None):
 
 
 def serving_measure(pkg, rate=5000.0, count=3000, budget=32 << 30, patterns_per_shape=64):
-    """cfg5 trace head: continuous batching server vs one request at a time.
+    """Head of the seeded serving trace (Poisson arrivals at `rate` per second, encode
+    and decode requests with n = 512..65536 at rates 1/2 and 3/4): continuous batching
+    server vs one request at a time.
 
     Both arms count each request's latency from its scheduled arrival
     (replay start + arrival time) to the moment its result is seen, so
@@ -661,7 +663,7 @@ def paper_route_measure(pkg, dev, reps=10):
 
 
 def serving_sweep(pkg, rates=(5000.0, 10000.0, 20000.0, 50000.0), count=3000):
-    """The cfg5 arrival rates, each on the head of its seeded trace, plus a
+    """The serving trace at 5 k to 50 k requests per second, each on the head of its seeded trace, plus a
     fresh-pattern variant (every decode request brings a new erasure pattern)."""
     runs = [serving_measure(pkg, rate=r, count=count) for r in rates]
     fresh = serving_measure(pkg, rate=rates[0], count=count, patterns_per_shape=1 << 30)

@@ -5,7 +5,7 @@
 // the zero-padded source), build its pattern tables (steps 1-3), decode every
 // codeword from the encoded matrix used as the receiver's slot buffer
 // (steps 4-6).  Groups with n >= 256 and the default root (every length of
-// the survey's ragged batch, up to 65536) all run in one launch of the ragged
+// the seeded ragged workload, 256 to 65536) all run in one launch of the ragged
 // persistent kernel (ragged_kernel.cu), each with its own pattern tables and
 // build scratch; the split-transform work items of the longest codes use a
 // scratch area per CTA.  Other groups (n < 256, another root, or the
